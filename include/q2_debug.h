@@ -1,0 +1,48 @@
+/*
+ * q2_debug.h -- introspection of the host schedules behind include/q2.h.
+ *
+ * These calls run on the host only (no device work) and expose the pass and
+ * group tables that q2_apply_pauli_rotations / q2_ansatz_create and
+ * q2_ham_create build, so that the schedule can be checked without a GPU.
+ * The paper has no counterpart: they describe this library's tiling of the
+ * state vector, not the method.
+ *
+ * Layouts (little endian, packed as below):
+ *   q2_pass   (136 bytes): uint64 w[13] local basis; uint64 umask; int32 T, C,
+ *             g_begin, g_end, rot_begin, rot_end.
+ *   q2_group  (112 bytes): uint64 bp[8] code basis in packed-index space;
+ *             uint32 xl, lut, rot0; uint8 kind, pivot, r, m; uint8 jcode[32].
+ * counts[0..2] = number of passes, groups, LUT entries.  Output arrays may be
+ * NULL (sizes only); otherwise they must hold counts[] entries.  lut2 holds
+ * two doubles per entry: (cos, sin) of the combined angle for rotation plans,
+ * (R, Q) combined coefficients for Hamiltonian plans.  signmask (rotation
+ * plans, n_rot entries): bit c set iff rotation k enters its group's angle
+ * with a minus sign at code c.
+ * Errors: Q2_ERR_INVALID for bad sizes or masks (see q2.h).
+ */
+#ifndef Q2_DEBUG_H
+#define Q2_DEBUG_H
+
+#include "q2.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+q2_status q2_debug_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z,
+                            const double *angles, int tile_qubits, int chunk_qubits,
+                            int64_t *counts, void *passes, void *groups, double *lut2,
+                            uint64_t *signmask);
+
+q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z,
+                            const double *coef, int tile_qubits, int chunk_qubits,
+                            int64_t *counts, void *passes, void *groups, double *lut2);
+
+/* Threads per CTA of the tile kernels (the per-thread offsets of q2_group.jcode use it). */
+int q2_debug_threads_per_cta(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* Q2_DEBUG_H */

@@ -1,0 +1,646 @@
+// C ABI (include/q2.h): argument checks, handles, schedules and launch order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/q2.h"
+#include "kernels.h"
+#include "q2_internal.h"
+
+using namespace q2;
+
+namespace {
+
+thread_local std::string g_err;
+
+q2_status fail(q2_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+q2_status cuda_fail(cudaError_t e, const char *where) {
+  return fail(e == cudaErrorMemoryAllocation ? Q2_ERR_OOM : Q2_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define Q2_CUDA(call, where)                     \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+int g_tile[2] = {12, 11};       // tile qubits per dtype
+const int g_chunk[2] = {4, 3};  // minimum contiguous low qubits per dtype (128-byte chunks)
+std::mutex g_cfg_mu;
+
+int amp_bytes(q2_dtype d) { return d == Q2_C64 ? 8 : 16; }
+int max_qubits(q2_dtype d) { return d == Q2_C64 ? 34 : 33; }
+
+bool valid_dtype(int d) { return d == Q2_C64 || d == Q2_C128; }
+
+q2_status check_n(int n, q2_dtype d) {
+  if (!valid_dtype(d)) return fail(Q2_ERR_INVALID, "unknown dtype");
+  if (n < 1 || n > max_qubits(d))
+    return fail(Q2_ERR_INVALID, "qubit count " + std::to_string(n) + " out of range");
+  return Q2_OK;
+}
+
+q2_status check_masks(int n, int64_t cnt, const uint64_t *x, const uint64_t *z, const char *what) {
+  if (cnt < 0) return fail(Q2_ERR_INVALID, std::string(what) + ": negative count");
+  if (cnt > 0 && (!x || !z)) return fail(Q2_ERR_INVALID, std::string(what) + ": NULL mask array");
+  const uint64_t bad = n >= 64 ? 0 : ~((1ull << n) - 1);
+  for (int64_t k = 0; k < cnt; ++k)
+    if ((x[k] | z[k]) & bad)
+      return fail(Q2_ERR_INVALID, std::string(what) + ": mask bit >= n at entry " + std::to_string(k));
+  return Q2_OK;
+}
+
+q2_status check_finite(int64_t cnt, const double *v, const char *what) {
+  if (cnt > 0 && !v) return fail(Q2_ERR_INVALID, std::string(what) + ": NULL array");
+  for (int64_t k = 0; k < cnt; ++k)
+    if (!std::isfinite(v[k]))
+      return fail(Q2_ERR_INVALID, std::string(what) + ": non-finite value at " + std::to_string(k));
+  return Q2_OK;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int tile_bits(q2_dtype d) {
+  std::lock_guard<std::mutex> g(g_cfg_mu);
+  return g_tile[d];
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device copies of a plan's groups (and optionally a LUT), owned by a handle.
+struct DevTables {
+  bool ready = false;
+  int device = -1;
+  int T = 0;
+  GroupDesc *groups = nullptr;
+  void *lut = nullptr;          // Hamiltonian LUT in the dtype's precision
+  uint64_t *signmask = nullptr; // rotation sign masks
+  void release() {
+    if (groups) cudaFree(groups);
+    if (lut) cudaFree(lut);
+    if (signmask) cudaFree(signmask);
+    groups = nullptr;
+    lut = nullptr;
+    signmask = nullptr;
+    ready = false;
+  }
+};
+
+// Convert an interleaved double LUT to the dtype's precision.
+std::vector<unsigned char> lut_bytes(const std::vector<double> &lut2, q2_dtype d) {
+  std::vector<unsigned char> out(lut2.size() * (d == Q2_C64 ? sizeof(float) : sizeof(double)));
+  if (d == Q2_C64) {
+    float *f = reinterpret_cast<float *>(out.data());
+    for (size_t i = 0; i < lut2.size(); ++i) f[i] = (float)lut2[i];
+  } else {
+    std::memcpy(out.data(), lut2.data(), lut2.size() * sizeof(double));
+  }
+  return out;
+}
+
+}  // namespace
+
+struct q2_ham {
+  int n = 0;
+  std::vector<uint64_t> x, z;
+  std::vector<double> c;
+  int64_t n_groups = 0;
+  HamPlan plan[2];
+  bool planned[2] = {false, false};
+  DevTables dev[2];
+  std::mutex mu;
+};
+
+struct q2_ansatz {
+  int n = 0, n_elec = 0;
+  int32_t n_params = 0;
+  std::vector<uint64_t> x, z;
+  std::vector<int32_t> param;
+  std::vector<double> coef;
+  RotPlan plan[2];
+  bool planned[2] = {false, false};
+  DevTables dev[2];
+  std::mutex mu;
+};
+
+namespace {
+
+q2_status ham_tables(const q2_ham *hc, q2_dtype d, const HamPlan **plan, const DevTables **dev) {
+  q2_ham *h = const_cast<q2_ham *>(hc);
+  std::lock_guard<std::mutex> g(h->mu);
+  if (!h->planned[d]) {
+    try {
+      h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
+                                  tile_bits(d), g_chunk[d]);
+    } catch (const std::exception &e) {
+      return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
+    }
+    h->planned[d] = true;
+  }
+  DevTables &t = h->dev[d];
+  int device = 0;
+  Q2_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+  if (t.ready && t.device != device) return fail(Q2_ERR_INVALID, "Hamiltonian handle used on another device");
+  if (!t.ready) {
+    const HamPlan &p = h->plan[d];
+    const size_t gb = sizeof(GroupDesc) * std::max<size_t>(1, p.groups.size());
+    std::vector<unsigned char> lb = lut_bytes(p.lut2, d);
+    Q2_CUDA(cudaMalloc(&t.groups, gb), "cudaMalloc(groups)");
+    if (cudaMalloc(&t.lut, std::max<size_t>(16, lb.size())) != cudaSuccess) {
+      t.release();
+      return fail(Q2_ERR_OOM, "cudaMalloc(Hamiltonian LUT)");
+    }
+    if (!p.groups.empty())
+      Q2_CUDA(cudaMemcpy(t.groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size(),
+                         cudaMemcpyHostToDevice), "upload groups");
+    if (!lb.empty()) Q2_CUDA(cudaMemcpy(t.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice), "upload LUT");
+    t.device = device;
+    t.T = p.T;
+    t.ready = true;
+  }
+  *plan = &h->plan[d];
+  *dev = &t;
+  return Q2_OK;
+}
+
+q2_status ansatz_tables(const q2_ansatz *ac, q2_dtype d, const RotPlan **plan, const DevTables **dev) {
+  q2_ansatz *a = const_cast<q2_ansatz *>(ac);
+  std::lock_guard<std::mutex> g(a->mu);
+  if (!a->planned[d]) {
+    try {
+      a->plan[d] = build_rot_plan(a->n, (int64_t)a->x.size(), a->x.data(), a->z.data(), tile_bits(d),
+                                  g_chunk[d]);
+    } catch (const std::exception &e) {
+      return fail(Q2_ERR_INVALID, std::string("rotation schedule: ") + e.what());
+    }
+    a->planned[d] = true;
+  }
+  if (!dev) {
+    *plan = &a->plan[d];
+    return Q2_OK;
+  }
+  DevTables &t = a->dev[d];
+  int device = 0;
+  Q2_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+  if (t.ready && t.device != device) return fail(Q2_ERR_INVALID, "ansatz handle used on another device");
+  if (!t.ready) {
+    const RotPlan &p = a->plan[d];
+    const size_t gb = sizeof(GroupDesc) * std::max<size_t>(1, p.groups.size());
+    const size_t sb = sizeof(uint64_t) * std::max<size_t>(1, p.signmask.size());
+    Q2_CUDA(cudaMalloc(&t.groups, gb), "cudaMalloc(groups)");
+    if (cudaMalloc(&t.signmask, sb) != cudaSuccess) {
+      t.release();
+      return fail(Q2_ERR_OOM, "cudaMalloc(sign masks)");
+    }
+    if (!p.groups.empty())
+      Q2_CUDA(cudaMemcpy(t.groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size(),
+                         cudaMemcpyHostToDevice), "upload groups");
+    if (!p.signmask.empty())
+      Q2_CUDA(cudaMemcpy(t.signmask, p.signmask.data(), sizeof(uint64_t) * p.signmask.size(),
+                         cudaMemcpyHostToDevice), "upload sign masks");
+    t.device = device;
+    t.T = p.T;
+    t.ready = true;
+  }
+  *plan = &a->plan[d];
+  *dev = &t;
+  return Q2_OK;
+}
+
+template <typename R>
+cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups, const void *dlut,
+                      bool inverse, cudaStream_t st) {
+  for (const PassDesc &pd : p.passes) {
+    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dlut, inverse, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t run_expect(const R *psi, int n, const HamPlan &h, const DevTables &t, double *partial,
+                       int grid, double *out2, cudaStream_t st) {
+  for (size_t i = 0; i < h.passes.size(); ++i) {
+    cudaError_t e = launch_expect<R>(psi, n, h.passes[i], t.groups, t.lut, partial, grid, i == 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_reduce_pairs(partial, grid, out2, st);
+}
+
+template <typename R>
+cudaError_t run_happly(const R *psi, R *lam, int n, const HamPlan &h, const DevTables &t, cudaStream_t st) {
+  for (size_t i = 0; i < h.passes.size(); ++i) {
+    cudaError_t e = launch_happly<R>(psi, lam, n, h.passes[i], t.groups, t.lut, i == 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int partial_doubles(int grad) {
+  const int blocks = max_grid_blocks(8, 12);
+  return grad ? blocks * RP_MAX : blocks * 2;
+}
+
+struct WsLayout {
+  size_t psi, lam, lut, gphi, partial, out, total;
+};
+
+WsLayout ws_layout(int n, q2_dtype d, int grad, int64_t lut_entries, int64_t n_rot) {
+  WsLayout L;
+  const size_t vec = (size_t)amp_bytes(d) << n;
+  size_t o = 0;
+  L.psi = o;
+  o = align_up(o + vec, 256);
+  L.lam = o;
+  if (grad) o = align_up(o + vec, 256);
+  L.lut = o;
+  o = align_up(o + (size_t)std::max<int64_t>(1, lut_entries) * amp_bytes(d), 256);
+  L.gphi = o;
+  if (grad) o = align_up(o + sizeof(double) * (size_t)std::max<int64_t>(1, n_rot), 256);
+  L.partial = o;
+  o = align_up(o + sizeof(double) * (size_t)partial_doubles(grad), 256);
+  L.out = o;
+  o = align_up(o + sizeof(double) * 4, 256);
+  L.total = o;
+  return L;
+}
+
+template <typename R>
+q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_dtype d, int want_grad,
+                   double *energy_out, double *grad_out, void *ws, size_t ws_bytes, cudaStream_t st) {
+  const RotPlan *rp;
+  const DevTables *rt;
+  q2_status s = ansatz_tables(a, d, &rp, &rt);
+  if (s != Q2_OK) return s;
+  const HamPlan *hp;
+  const DevTables *ht;
+  if ((s = ham_tables(h, d, &hp, &ht)) != Q2_OK) return s;
+  const int n = a->n;
+  const WsLayout L = ws_layout(n, d, want_grad, rp->lut_entries, (int64_t)a->x.size());
+  if (ws_bytes < L.total) return fail(Q2_ERR_INVALID, "workspace too small");
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  R *psi = reinterpret_cast<R *>(base + L.psi);
+  R *lam = reinterpret_cast<R *>(base + L.lam);
+  double *gphi = reinterpret_cast<double *>(base + L.gphi);
+  double *partial = reinterpret_cast<double *>(base + L.partial);
+  double *out = reinterpret_cast<double *>(base + L.out);
+
+  // angles and the per-call LUT (host, double precision)
+  const size_t nrot = a->x.size();
+  std::vector<double> phi(nrot);
+  for (size_t k = 0; k < nrot; ++k) phi[k] = a->coef[k] * theta[a->param[k]];
+  std::vector<double> lut2(2 * (size_t)std::max<int64_t>(1, rp->lut_entries));
+  rp->build_lut(phi.data(), lut2.data());
+  std::vector<unsigned char> lb = lut_bytes(lut2, d);
+  Q2_CUDA(cudaMemcpyAsync(base + L.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice, st), "upload LUT");
+
+  Q2_CUDA(launch_init_hf<R>(psi, n, a->n_elec, st), "init_hf");
+  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, base + L.lut, false, st), "sweep");
+  double host_out[2] = {0, 0};
+  if (!want_grad) {
+    const int grid = expect_grid<R>(n, hp->T, std::min(g_chunk[d], hp->T));
+    Q2_CUDA(run_expect<R>(psi, n, *hp, *ht, partial, grid, out, st), "expectation");
+    Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
+    Q2_CUDA(cudaStreamSynchronize(st), "sync");
+    *energy_out = host_out[0] / host_out[1];
+    return Q2_OK;
+  }
+  Q2_CUDA(run_happly<R>(psi, lam, n, *hp, *ht, st), "H apply");
+  const int dgrid = dot_grid<R>(n);
+  Q2_CUDA(launch_dot<R>(psi, lam, n, partial, dgrid, st), "dot");
+  Q2_CUDA(launch_reduce_pairs(partial, dgrid, out, st), "reduce");
+  for (size_t i = rp->passes.size(); i-- > 0;) {
+    Q2_CUDA(launch_reverse<R>(psi, lam, n, rp->passes[i], rt->groups, base + L.lut, rt->signmask,
+                              partial, gphi, st), "reverse sweep");
+  }
+  std::vector<double> g(nrot);
+  Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
+  if (nrot) Q2_CUDA(cudaMemcpyAsync(g.data(), gphi, sizeof(double) * nrot, cudaMemcpyDeviceToHost, st), "D2H");
+  Q2_CUDA(cudaStreamSynchronize(st), "sync");
+  *energy_out = host_out[0] / host_out[1];
+  for (int p = 0; p < a->n_params; ++p) grad_out[p] = 0.0;
+  for (size_t k = 0; k < nrot; ++k) grad_out[a->param[k]] += a->coef[k] * g[k];
+  return Q2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int q2_version(void) { return 100; }
+
+const char *q2_last_error(void) { return g_err.c_str(); }
+
+q2_status q2_set_tile_qubits(q2_dtype dtype, int tile_qubits) {
+  if (!valid_dtype(dtype)) return fail(Q2_ERR_INVALID, "unknown dtype");
+  // the reverse sweep holds two tiles: 2 * 2^T * 16 bytes must stay within shared memory
+  const int tmax = dtype == Q2_C64 ? T_LIMIT : T_LIMIT - 1;
+  if (tile_qubits < T_MIN || tile_qubits > tmax) return fail(Q2_ERR_INVALID, "tile qubits out of range");
+  std::lock_guard<std::mutex> g(g_cfg_mu);
+  g_tile[dtype] = tile_qubits;
+  return Q2_OK;
+}
+
+q2_status q2_state_init_hf(void *psi_dev, int n, int n_elec, q2_dtype dtype, void *stream) {
+  q2_status s = check_n(n, dtype);
+  if (s != Q2_OK) return s;
+  if (n_elec < 0 || n_elec > n) return fail(Q2_ERR_INVALID, "n_elec out of range");
+  if (!psi_dev || !aligned(psi_dev, 16)) return fail(Q2_ERR_INVALID, "psi must be a 16-byte aligned device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = dtype == Q2_C64 ? launch_init_hf<float>(static_cast<float *>(psi_dev), n, n_elec, st)
+                                  : launch_init_hf<double>(static_cast<double *>(psi_dev), n, n_elec, st);
+  if (e != cudaSuccess) return cuda_fail(e, "init_hf");
+  return Q2_OK;
+}
+
+q2_status q2_apply_pauli_rotations(void *psi_dev, int n, q2_dtype dtype, const uint64_t *xmask,
+                                   const uint64_t *zmask, const double *angles, int64_t n_rot,
+                                   void *stream) {
+  q2_status s = check_n(n, dtype);
+  if (s != Q2_OK) return s;
+  if (!psi_dev || !aligned(psi_dev, 16)) return fail(Q2_ERR_INVALID, "psi must be a 16-byte aligned device pointer");
+  if ((s = check_masks(n, n_rot, xmask, zmask, "rotations")) != Q2_OK) return s;
+  if ((s = check_finite(n_rot, angles, "angles")) != Q2_OK) return s;
+  if (n_rot == 0) return Q2_OK;
+  RotPlan p;
+  try {
+    p = build_rot_plan(n, n_rot, xmask, zmask, tile_bits(dtype), g_chunk[dtype]);
+  } catch (const std::exception &e) {
+    return fail(Q2_ERR_INVALID, std::string("rotation schedule: ") + e.what());
+  }
+  std::vector<double> lut2(2 * (size_t)std::max<int64_t>(1, p.lut_entries));
+  p.build_lut(angles, lut2.data());
+  std::vector<unsigned char> lb = lut_bytes(lut2, dtype);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t gb = align_up(sizeof(GroupDesc) * p.groups.size(), 256);
+  unsigned char *tmp = nullptr;
+  Q2_CUDA(cudaMallocAsync((void **)&tmp, gb + lb.size(), st), "cudaMallocAsync(schedule)");
+  cudaError_t e = cudaMemcpyAsync(tmp, p.groups.data(), sizeof(GroupDesc) * p.groups.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + gb, lb.data(), lb.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    const GroupDesc *dg = reinterpret_cast<const GroupDesc *>(tmp);
+    e = dtype == Q2_C64 ? run_sweep<float>(static_cast<float *>(psi_dev), n, p, dg, tmp + gb, false, st)
+                        : run_sweep<double>(static_cast<double *>(psi_dev), n, p, dg, tmp + gb, false, st);
+  }
+  cudaFreeAsync(tmp, st);
+  if (e != cudaSuccess) return cuda_fail(e, "apply_pauli_rotations");
+  return Q2_OK;
+}
+
+q2_status q2_ham_create(int n, const uint64_t *x, const uint64_t *z, const double *coef, int64_t n_terms,
+                        q2_ham **out) {
+  if (!out) return fail(Q2_ERR_INVALID, "NULL output handle");
+  *out = nullptr;
+  if (n < 1 || n > 34) return fail(Q2_ERR_INVALID, "qubit count out of range");
+  q2_status s = check_masks(n, n_terms, x, z, "Hamiltonian");
+  if (s != Q2_OK) return s;
+  if ((s = check_finite(n_terms, coef, "coefficients")) != Q2_OK) return s;
+  q2_ham *h = new (std::nothrow) q2_ham;
+  if (!h) return fail(Q2_ERR_OOM, "host allocation");
+  h->n = n;
+  h->x.assign(x, x + n_terms);
+  h->z.assign(z, z + n_terms);
+  h->c.assign(coef, coef + n_terms);
+  h->n_groups = count_x_groups(n_terms, x);
+  *out = h;
+  return Q2_OK;
+}
+
+q2_status q2_ham_destroy(q2_ham *ham) {
+  if (!ham) return Q2_OK;
+  ham->dev[0].release();
+  ham->dev[1].release();
+  delete ham;
+  return Q2_OK;
+}
+
+q2_status q2_ham_info(const q2_ham *ham, int64_t *n_terms, int64_t *n_groups) {
+  if (!ham) return fail(Q2_ERR_INVALID, "NULL handle");
+  if (n_terms) *n_terms = (int64_t)ham->c.size();
+  if (n_groups) *n_groups = ham->n_groups;
+  return Q2_OK;
+}
+
+q2_status q2_expectation(const void *psi_dev, int n, q2_dtype dtype, const q2_ham *ham, double *energy_out,
+                         double *norm_out, void *stream) {
+  q2_status s = check_n(n, dtype);
+  if (s != Q2_OK) return s;
+  if (!ham || !energy_out) return fail(Q2_ERR_INVALID, "NULL argument");
+  if (ham->n != n) return fail(Q2_ERR_INVALID, "Hamiltonian qubit count differs from n");
+  if (!psi_dev || !aligned(psi_dev, 16)) return fail(Q2_ERR_INVALID, "psi must be a 16-byte aligned device pointer");
+  const HamPlan *hp;
+  const DevTables *ht;
+  if ((s = ham_tables(ham, dtype, &hp, &ht)) != Q2_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int C = std::min(g_chunk[dtype], hp->T);
+  const int grid = dtype == Q2_C64 ? expect_grid<float>(n, hp->T, C) : expect_grid<double>(n, hp->T, C);
+  double *tmp = nullptr;
+  Q2_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * (2 * (size_t)grid + 2), st), "cudaMallocAsync(partials)");
+  double host_out[2] = {0, 0};
+  cudaError_t e =
+      dtype == Q2_C64
+          ? run_expect<float>(static_cast<const float *>(psi_dev), n, *hp, *ht, tmp, grid, tmp + 2 * grid, st)
+          : run_expect<double>(static_cast<const double *>(psi_dev), n, *hp, *ht, tmp, grid, tmp + 2 * grid, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp + 2 * grid, sizeof(host_out), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(tmp, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "expectation");
+  *energy_out = host_out[0] / host_out[1];
+  if (norm_out) *norm_out = host_out[1];
+  return Q2_OK;
+}
+
+q2_status q2_apply_hamiltonian(const void *psi_dev, void *lam_dev, int n, q2_dtype dtype, const q2_ham *ham,
+                               void *stream) {
+  q2_status s = check_n(n, dtype);
+  if (s != Q2_OK) return s;
+  if (!ham) return fail(Q2_ERR_INVALID, "NULL Hamiltonian");
+  if (ham->n != n) return fail(Q2_ERR_INVALID, "Hamiltonian qubit count differs from n");
+  if (!psi_dev || !lam_dev || !aligned(psi_dev, 16) || !aligned(lam_dev, 16))
+    return fail(Q2_ERR_INVALID, "psi and lambda must be 16-byte aligned device pointers");
+  if (psi_dev == lam_dev) return fail(Q2_ERR_INVALID, "psi and lambda must be distinct buffers");
+  const HamPlan *hp;
+  const DevTables *ht;
+  if ((s = ham_tables(ham, dtype, &hp, &ht)) != Q2_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = dtype == Q2_C64
+                      ? run_happly<float>(static_cast<const float *>(psi_dev), static_cast<float *>(lam_dev), n, *hp, *ht, st)
+                      : run_happly<double>(static_cast<const double *>(psi_dev), static_cast<double *>(lam_dev), n, *hp, *ht, st);
+  if (e != cudaSuccess) return cuda_fail(e, "apply_hamiltonian");
+  return Q2_OK;
+}
+
+q2_status q2_ansatz_create(int n, int n_elec, int64_t n_rot, const uint64_t *x, const uint64_t *z,
+                           const int32_t *param_idx, const double *coef, int32_t n_params, q2_ansatz **out) {
+  if (!out) return fail(Q2_ERR_INVALID, "NULL output handle");
+  *out = nullptr;
+  if (n < 1 || n > 34) return fail(Q2_ERR_INVALID, "qubit count out of range");
+  if (n_elec < 0 || n_elec > n) return fail(Q2_ERR_INVALID, "n_elec out of range");
+  if (n_params < 0) return fail(Q2_ERR_INVALID, "negative parameter count");
+  q2_status s = check_masks(n, n_rot, x, z, "ansatz");
+  if (s != Q2_OK) return s;
+  if ((s = check_finite(n_rot, coef, "ansatz coefficients")) != Q2_OK) return s;
+  if (n_rot > 0 && !param_idx) return fail(Q2_ERR_INVALID, "NULL parameter index array");
+  for (int64_t k = 0; k < n_rot; ++k)
+    if (param_idx[k] < 0 || param_idx[k] >= n_params)
+      return fail(Q2_ERR_INVALID, "parameter index out of range at " + std::to_string(k));
+  q2_ansatz *a = new (std::nothrow) q2_ansatz;
+  if (!a) return fail(Q2_ERR_OOM, "host allocation");
+  a->n = n;
+  a->n_elec = n_elec;
+  a->n_params = n_params;
+  a->x.assign(x, x + n_rot);
+  a->z.assign(z, z + n_rot);
+  a->param.assign(param_idx, param_idx + n_rot);
+  a->coef.assign(coef, coef + n_rot);
+  *out = a;
+  return Q2_OK;
+}
+
+q2_status q2_ansatz_destroy(q2_ansatz *ansatz) {
+  if (!ansatz) return Q2_OK;
+  ansatz->dev[0].release();
+  ansatz->dev[1].release();
+  delete ansatz;
+  return Q2_OK;
+}
+
+q2_status q2_ansatz_info(const q2_ansatz *ansatz, q2_dtype dtype, int64_t *n_passes, int64_t *n_groups) {
+  if (!ansatz) return fail(Q2_ERR_INVALID, "NULL handle");
+  if (!valid_dtype(dtype)) return fail(Q2_ERR_INVALID, "unknown dtype");
+  const RotPlan *rp;
+  q2_status s = ansatz_tables(ansatz, dtype, &rp, nullptr);
+  if (s != Q2_OK) return s;
+  if (n_passes) *n_passes = (int64_t)rp->passes.size();
+  if (n_groups) *n_groups = (int64_t)rp->groups.size();
+  return Q2_OK;
+}
+
+size_t q2_vqe_workspace_bytes(const q2_ansatz *ansatz, q2_dtype dtype, int want_grad) {
+  if (!ansatz || !valid_dtype(dtype)) return 0;
+  const RotPlan *rp;
+  if (ansatz_tables(ansatz, dtype, &rp, nullptr) != Q2_OK) return 0;
+  return ws_layout(ansatz->n, dtype, want_grad ? 1 : 0, rp->lut_entries, (int64_t)ansatz->x.size()).total;
+}
+
+q2_status q2_vqe_energy_grad(const q2_ansatz *ansatz, const q2_ham *ham, const double *theta, q2_dtype dtype,
+                             int want_grad, double *energy_out, double *grad_out, void *workspace_dev,
+                             size_t workspace_bytes, void *stream) {
+  if (!ansatz || !ham || !energy_out) return fail(Q2_ERR_INVALID, "NULL argument");
+  q2_status s = check_n(ansatz->n, dtype);
+  if (s != Q2_OK) return s;
+  if (ham->n != ansatz->n) return fail(Q2_ERR_INVALID, "Hamiltonian and ansatz qubit counts differ");
+  if ((s = check_finite(ansatz->n_params, theta, "theta")) != Q2_OK) return s;
+  if (want_grad && !grad_out) return fail(Q2_ERR_INVALID, "NULL gradient output");
+  if (!workspace_dev || !aligned(workspace_dev, 256))
+    return fail(Q2_ERR_INVALID, "workspace must be a 256-byte aligned device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return dtype == Q2_C64 ? vqe_impl<float>(ansatz, ham, theta, dtype, want_grad ? 1 : 0, energy_out, grad_out,
+                                           workspace_dev, workspace_bytes, st)
+                         : vqe_impl<double>(ansatz, ham, theta, dtype, want_grad ? 1 : 0, energy_out, grad_out,
+                                            workspace_dev, workspace_bytes, st);
+}
+
+size_t q2_batch_workspace_bytes(int n_requests, const q2_ansatz *const *ansatz, const q2_ham *const *ham,
+                                q2_dtype dtype) {
+  (void)n_requests;
+  (void)ansatz;
+  (void)ham;
+  (void)dtype;
+  return 0;
+}
+
+q2_status q2_batch_energy_grad(int n_requests, const q2_ansatz *const *ansatz, const q2_ham *const *ham,
+                               const double *const *theta, const int *want_grad, q2_dtype dtype,
+                               double *energy_out, double *const *grad_out, void *workspace_dev,
+                               size_t workspace_bytes, void *stream) {
+  (void)n_requests;
+  (void)ansatz;
+  (void)ham;
+  (void)theta;
+  (void)want_grad;
+  (void)dtype;
+  (void)energy_out;
+  (void)grad_out;
+  (void)workspace_dev;
+  (void)workspace_bytes;
+  (void)stream;
+  return fail(Q2_ERR_UNSUPPORTED, "batched small-state path not built yet");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ schedule introspection
+
+#include "../../include/q2_debug.h"
+
+static_assert(sizeof(PassDesc) == 136, "q2_pass layout");
+
+extern "C" {
+
+q2_status q2_debug_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, const double *angles,
+                            int tile_qubits, int chunk_qubits, int64_t *counts, void *passes, void *groups,
+                            double *lut2, uint64_t *signmask) {
+  if (n < 1 || n > 34 || !counts) return fail(Q2_ERR_INVALID, "bad arguments");
+  if (tile_qubits < 1 || tile_qubits > T_LIMIT || chunk_qubits < 1) return fail(Q2_ERR_INVALID, "bad tile shape");
+  q2_status s = check_masks(n, n_rot, x, z, "rotations");
+  if (s != Q2_OK) return s;
+  RotPlan p;
+  try {
+    p = build_rot_plan(n, n_rot, x, z, tile_qubits, chunk_qubits);
+  } catch (const std::exception &e) {
+    return fail(Q2_ERR_INVALID, e.what());
+  }
+  counts[0] = (int64_t)p.passes.size();
+  counts[1] = (int64_t)p.groups.size();
+  counts[2] = p.lut_entries;
+  if (passes) std::memcpy(passes, p.passes.data(), sizeof(PassDesc) * p.passes.size());
+  if (groups) std::memcpy(groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size());
+  if (lut2) {
+    if ((s = check_finite(n_rot, angles, "angles")) != Q2_OK) return s;
+    p.build_lut(angles, lut2);
+  }
+  if (signmask) std::memcpy(signmask, p.signmask.data(), sizeof(uint64_t) * p.signmask.size());
+  return Q2_OK;
+}
+
+q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z, const double *coef,
+                            int tile_qubits, int chunk_qubits, int64_t *counts, void *passes, void *groups,
+                            double *lut2) {
+  if (n < 1 || n > 34 || !counts) return fail(Q2_ERR_INVALID, "bad arguments");
+  if (tile_qubits < 1 || tile_qubits > T_LIMIT || chunk_qubits < 1) return fail(Q2_ERR_INVALID, "bad tile shape");
+  q2_status s = check_masks(n, n_terms, x, z, "Hamiltonian");
+  if (s != Q2_OK) return s;
+  if ((s = check_finite(n_terms, coef, "coefficients")) != Q2_OK) return s;
+  HamPlan p;
+  try {
+    p = build_ham_plan(n, n_terms, x, z, coef, tile_qubits, chunk_qubits);
+  } catch (const std::exception &e) {
+    return fail(Q2_ERR_INVALID, e.what());
+  }
+  counts[0] = (int64_t)p.passes.size();
+  counts[1] = (int64_t)p.groups.size();
+  counts[2] = p.lut_entries;
+  if (passes) std::memcpy(passes, p.passes.data(), sizeof(PassDesc) * p.passes.size());
+  if (groups) std::memcpy(groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size());
+  if (lut2) std::memcpy(lut2, p.lut2.data(), sizeof(double) * p.lut2.size());
+  return Q2_OK;
+}
+
+int q2_debug_threads_per_cta(void) { return NT; }
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal definitions shared by the host scheduler and the tile kernels.
+//
+// Tiling.  A pass works on tiles of 2^T amplitudes.  Its local space is a
+// T-dimensional GF(2) subspace W of index space spanned by w_0..w_{T-1},
+// with w_b = e_b for b < C (so a tile is made of contiguous 2^C-amplitude
+// chunks) and every other w_b free of the low C bits.  Tiles are the cosets
+// of W: tile t, local index l is the amplitude
+//     i = deposit(t, umask) ^ (XOR_{b: l_b = 1} w_b),
+// where umask holds the n - T qubit positions that are not pivots of W.  A
+// rotation or Hamiltonian term with xmask x in W maps every tile onto itself,
+// so a pass may hold any run of groups whose xmasks span at most T dimensions
+// together with e_0..e_{C-1}: one new dimension per new xmask, however many
+// qubits that xmask touches.  parity(i & z) = parity(packed & packz(z)) with
+// packed = (t << T) | l and packz(z) = (extract(z, umask) << T) |
+// sum_b parity(w_b & z) << b.
+//
+// Groups.  Consecutive rotations with the same xmask and the same parity of
+// popcount(x & z) commute (their strings agree on every qubit where both
+// have X or Y, and differ on an even number of X/Y-vs-Y/X positions), so on
+// each amplitude pair {i, i ^ x} their product is one 2x2 rotation whose
+// angle is a signed sum of the group's angles.  The sign pattern depends on
+// i only through the parities parity(i & b_l) for a basis b_1..b_r of the
+// group's zmasks: the r-bit "code".  A per-group look-up table (LUT) of
+// 2^r entries holds cos/sin of the combined angle for every code, computed
+// on the host in double precision.  Hamiltonian terms sharing an xmask are
+// grouped the same way: the LUT then holds the combined coefficients
+// (R, Q) of the pair {i, i^x} for every code.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace q2 {
+
+constexpr int NT = 256;          // threads per CTA of the tile kernels
+constexpr int R_MAX = 8;         // max code bits of a Hamiltonian group
+constexpr int R_MAX_ROT = 6;     // max code bits of a rotation group (sign masks fit 64 bits)
+constexpr int M_MAX = 16;        // max rotations in one rotation group
+constexpr int P_MAX = 32;        // max per-thread iterations over a tile (2^T <= NT * P_MAX)
+constexpr int RP_MAX = 512;      // max rotations in one pass (reverse-sweep partials)
+constexpr int T_MIN = 8;
+constexpr int T_LIMIT = 13;
+
+enum : uint8_t { KIND_DIAG = 0, KIND_REAL = 1, KIND_XROT = 2, KIND_PAIR = 3 };
+
+// One group as the kernels read it (uniform across a CTA, read through L1).
+struct alignas(16) GroupDesc {
+  uint64_t bp[R_MAX];     // code basis in packed-index space
+  uint32_t xl;            // xmask in local-index space (0 for diagonal groups)
+  uint32_t lut;           // first LUT entry of this group
+  uint32_t rot0;          // rotation groups: first rotation, relative to the pass
+  uint8_t kind;           // KIND_*
+  uint8_t pivot;          // local bit removed to enumerate pairs (highest bit of xl)
+  uint8_t r;              // code bits; the LUT has 2^r entries
+  uint8_t m;              // rotation groups: number of rotations
+  uint8_t jcode[P_MAX];   // code of the j-th per-thread offset (NT * j, pivot-inserted)
+};
+static_assert(sizeof(GroupDesc) == 112, "GroupDesc layout");
+
+struct PassDesc {
+  uint64_t w[T_LIMIT];    // local basis; w[b] = e_b for b < C
+  uint64_t umask;         // tile-index qubit positions
+  int T;                  // local dimension
+  int C;                  // chunk = 2^C contiguous amplitudes
+  int g_begin, g_end;     // groups [g_begin, g_end)
+  int rot_begin, rot_end; // rotation plans: rotations covered by this pass
+};
+
+// Host-side schedule of a rotation list (an ansatz or one apply call).
+struct RotPlan {
+  int n = 0;
+  int T = 0;
+  std::vector<PassDesc> passes;
+  std::vector<GroupDesc> groups;       // device image
+  std::vector<int> grp_rot_begin;      // rotations of group g: [begin, begin + m)
+  std::vector<uint8_t> rot_coord;      // per rotation: z_k in the group's code basis
+  std::vector<int8_t> rot_sigma;       // per rotation: fixed sign of its angle in the LUT
+  std::vector<uint64_t> signmask;      // per rotation: bit c set iff its sign at code c is -1
+  int64_t lut_entries = 0;
+  int max_pass_rots = 0;
+  // LUT of (cos b, sin b) for every group and code, b = sum_k sign_k(code) phi_k / 2.
+  void build_lut(const double *phi, double *lut2) const;
+};
+
+// Host-side schedule of a Hamiltonian.
+struct HamPlan {
+  int n = 0;
+  int T = 0;
+  std::vector<PassDesc> passes;
+  std::vector<GroupDesc> groups;
+  std::vector<double> lut2;            // (R, Q) per group and code
+  int64_t lut_entries = 0;
+};
+
+RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, int T, int C);
+HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z,
+                       const double *c, int T, int C);
+int64_t count_x_groups(int64_t n_terms, const uint64_t *x);
+
+// ---- bit helpers (host and device)
+#if defined(__CUDACC__)
+#define Q2_HD __host__ __device__ __forceinline__
+#else
+#define Q2_HD inline
+#endif
+
+Q2_HD uint64_t deposit_bits(uint64_t v, uint64_t mask) {
+  uint64_t out = 0;
+  while (mask) {
+    uint64_t low = mask & (~mask + 1);
+    if (v & 1) out |= low;
+    v >>= 1;
+    mask &= mask - 1;
+  }
+  return out;
+}
+
+Q2_HD uint64_t extract_bits(uint64_t v, uint64_t mask) {
+  uint64_t out = 0;
+  int k = 0;
+  while (mask) {
+    uint64_t low = mask & (~mask + 1);
+    if (v & low) out |= (uint64_t)1 << k;
+    ++k;
+    mask &= mask - 1;
+  }
+  return out;
+}
+
+Q2_HD uint32_t insert_zero(uint32_t q, int p) {
+  uint32_t lo = q & ((1u << p) - 1u);
+  return ((q >> p) << (p + 1)) | lo;
+}
+
+}  // namespace q2

@@ -1,0 +1,460 @@
+// Host schedulers: rotation lists and Hamiltonians -> tile passes + groups.
+//
+// Rotation lists keep their order (the circuit order of the product formula
+// after Eq. ucc); only runs of consecutive, mutually commuting rotations with
+// the same xmask are merged into one group, and consecutive groups whose
+// xmasks span at most T dimensions (with the low chunk qubits) share one pass
+// over HBM.
+//
+// Hamiltonian terms may be visited in any order (Eq. qubit-ham-detail is a
+// plain sum), so their xmask groups are packed into passes greedily, on tiles
+// spanned by unit qubit vectors, to minimise the number of passes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+
+#include "q2_internal.h"
+
+namespace q2 {
+
+namespace {
+
+inline int popc64(uint64_t v) { return __builtin_popcountll(v); }
+inline int parity64(uint64_t v) { return __builtin_parityll(v); }
+inline int high_bit(uint64_t v) { return 63 - __builtin_clzll(v); }
+
+// GF(2) span of a few vectors, with the coordinates of any member in terms of
+// the inserted (original) basis vectors.
+struct Gf2Basis {
+  std::vector<uint64_t> orig;   // basis vectors as inserted
+  std::vector<uint64_t> red;    // reduced rows, distinct highest bits, descending
+  std::vector<uint32_t> comb;   // red[i] = XOR of orig[l] over bits l of comb[i]
+
+  int rank() const { return (int)orig.size(); }
+
+  uint64_t reduce(uint64_t v, uint32_t &c) const {
+    c = 0;
+    for (size_t i = 0; i < red.size(); ++i) {
+      if ((v >> high_bit(red[i])) & 1) {
+        v ^= red[i];
+        c ^= comb[i];
+      }
+    }
+    return v;
+  }
+  bool contains(uint64_t v) const {
+    uint32_t c;
+    return reduce(v, c) == 0;
+  }
+  uint32_t coords(uint64_t v) const {
+    uint32_t c;
+    if (reduce(v, c) != 0) throw std::logic_error("coords of a vector outside the span");
+    return c;
+  }
+  bool add(uint64_t v) {
+    uint32_t c;
+    uint64_t rem = reduce(v, c);
+    if (rem == 0) return false;
+    int l = (int)orig.size();
+    orig.push_back(v);
+    uint32_t cc = c ^ (1u << l);
+    int hb = high_bit(rem);
+    size_t pos = 0;
+    while (pos < red.size() && high_bit(red[pos]) > hb) ++pos;
+    red.insert(red.begin() + pos, rem);
+    comb.insert(comb.begin() + pos, cc);
+    return true;
+  }
+  uint64_t pivot_mask() const {
+    uint64_t m = 0;
+    for (uint64_t r : red) m |= 1ull << high_bit(r);
+    return m;
+  }
+};
+
+struct RawGroup {
+  uint64_t x;
+  uint8_t kind;
+  std::vector<int64_t> members;   // term / rotation indices
+  Gf2Basis basis;                 // span of the members' zmasks
+};
+
+uint64_t nmask_of(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
+
+// Local basis of a pass: e_0..e_{C-1} first (C as large as the span allows),
+// then the generators reduced modulo the low unit vectors, filled up to T
+// dimensions with the lowest independent unit vectors.
+struct Tiling {
+  uint64_t w[T_LIMIT];
+  uint64_t umask;
+  int T, C;
+  Gf2Basis wb;   // basis w_0..w_{T-1} in order, for coordinates
+
+  uint64_t packz(uint64_t z) const {
+    uint64_t lo = 0;
+    for (int b = 0; b < T; ++b) lo |= (uint64_t)parity64(w[b] & z) << b;
+    return (extract_bits(z, umask) << T) | lo;
+  }
+  uint32_t local_coords(uint64_t x) const { return wb.coords(x); }
+};
+
+Tiling make_tiling(int n, int T, int Cmin, const std::vector<uint64_t> &gens) {
+  Gf2Basis span;
+  for (int q = 0; q < Cmin; ++q) span.add(1ull << q);
+  for (uint64_t g : gens) span.add(g);
+  if (span.rank() > T) throw std::logic_error("pass generators exceed the tile dimension");
+  for (int q = 0; q < n && span.rank() < T; ++q) span.add(1ull << q);
+  int C = 0;
+  while (C < T && C < n && span.contains(1ull << C)) ++C;
+  Tiling t;
+  std::memset(t.w, 0, sizeof(t.w));
+  t.T = T;
+  t.C = C;
+  const uint64_t low = (C >= 64) ? ~0ull : ((1ull << C) - 1);
+  for (int b = 0; b < C; ++b) {
+    t.w[b] = 1ull << b;
+    t.wb.add(t.w[b]);
+  }
+  int b = C;
+  for (uint64_t v : span.orig) {
+    if (b >= T) break;
+    uint64_t r = v & ~low;
+    if (r == 0) continue;
+    if (t.wb.add(r)) t.w[b++] = r;
+  }
+  if (b != T) throw std::logic_error("tiling basis incomplete");
+  t.umask = nmask_of(n) & ~t.wb.pivot_mask();
+  return t;
+}
+
+// Device descriptor of one group inside a pass.
+GroupDesc make_desc(const RawGroup &g, const Tiling &tl, uint32_t lut_off) {
+  GroupDesc d;
+  std::memset(&d, 0, sizeof(d));
+  const int T = tl.T;
+  d.kind = g.kind;
+  d.r = (uint8_t)g.basis.rank();
+  d.lut = lut_off;
+  for (int l = 0; l < d.r; ++l) d.bp[l] = tl.packz(g.basis.orig[l]);
+  const bool diag = (g.kind == KIND_DIAG);
+  d.xl = diag ? 0u : tl.local_coords(g.x);
+  d.pivot = diag ? 0 : (uint8_t)high_bit(d.xl);
+  const int64_t per_tile = diag ? (1ll << T) : (1ll << (T - 1));
+  const int64_t P = std::max<int64_t>(1, per_tile / NT);
+  if (P > P_MAX) throw std::logic_error("tile too large for the per-thread offset table");
+  const uint64_t local_mask = (1ull << T) - 1;
+  for (int64_t j = 0; j < P; ++j) {
+    uint32_t v = (uint32_t)(NT * j);
+    if (!diag) v = insert_zero(v, d.pivot);
+    uint32_t code = 0;
+    for (int l = 0; l < d.r; ++l) code |= (uint32_t)parity64(v & d.bp[l] & local_mask) << l;
+    d.jcode[j] = (uint8_t)code;
+  }
+  return d;
+}
+
+PassDesc make_pass(const Tiling &tl) {
+  PassDesc pd;
+  std::memset(&pd, 0, sizeof(pd));
+  for (int b = 0; b < T_LIMIT; ++b) pd.w[b] = tl.w[b];
+  pd.umask = tl.umask;
+  pd.T = tl.T;
+  pd.C = tl.C;
+  return pd;
+}
+
+}  // namespace
+
+int64_t count_x_groups(int64_t n_terms, const uint64_t *x) {
+  std::vector<uint64_t> v(x, x + n_terms);
+  std::sort(v.begin(), v.end());
+  return (int64_t)(std::unique(v.begin(), v.end()) - v.begin());
+}
+
+// --------------------------------------------------------------- rotations
+
+RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, int Tmax,
+                       int Cmin) {
+  RotPlan P;
+  P.n = n;
+  const int T = std::min(Tmax, n);
+  P.T = T;
+  const int C = std::min(Cmin, T);
+
+  // 1. groups of consecutive commuting rotations with one xmask
+  std::vector<RawGroup> groups;
+  for (int64_t k = 0; k < n_rot; ++k) {
+    const int ny = popc64(x[k] & z[k]);
+    const uint8_t kind = x[k] == 0 ? KIND_DIAG : ((ny & 1) ? KIND_REAL : KIND_XROT);
+    bool join = false;
+    if (!groups.empty()) {
+      RawGroup &g = groups.back();
+      if (g.x == x[k] && g.kind == kind && (int)g.members.size() < M_MAX &&
+          (g.basis.contains(z[k]) || g.basis.rank() < R_MAX_ROT))
+        join = true;
+    }
+    if (!join) {
+      groups.emplace_back();
+      groups.back().x = x[k];
+      groups.back().kind = kind;
+    }
+    groups.back().members.push_back(k);
+    groups.back().basis.add(z[k]);
+  }
+
+  // 2. passes: consecutive groups whose xmasks span <= T dimensions with e_0..e_{C-1}
+  struct PassRange {
+    size_t gb, ge;
+    std::vector<uint64_t> gens;
+  };
+  std::vector<PassRange> ranges;
+  {
+    Gf2Basis W;
+    for (int q = 0; q < C; ++q) W.add(1ull << q);
+    PassRange cur{0, 0, {}};
+    int rots = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      const uint64_t xg = groups[g].x;
+      const int m = (int)groups[g].members.size();
+      const bool fits = (xg == 0 || W.contains(xg) || W.rank() < T) && rots + m <= RP_MAX;
+      if (!fits && g > cur.gb) {
+        cur.ge = g;
+        ranges.push_back(cur);
+        cur = PassRange{g, 0, {}};
+        W = Gf2Basis();
+        for (int q = 0; q < C; ++q) W.add(1ull << q);
+        rots = 0;
+      }
+      if (xg != 0 && W.add(xg)) cur.gens.push_back(xg);
+      rots += m;
+    }
+    if (cur.gb < groups.size()) {
+      cur.ge = groups.size();
+      ranges.push_back(cur);
+    }
+  }
+
+  // 3. descriptors
+  P.rot_coord.resize(n_rot);
+  P.rot_sigma.resize(n_rot);
+  P.signmask.resize(n_rot);
+  uint32_t lut = 0;
+  for (const PassRange &pr : ranges) {
+    const Tiling tl = make_tiling(n, T, C, pr.gens);
+    PassDesc pd = make_pass(tl);
+    pd.g_begin = (int)P.groups.size();
+    pd.rot_begin = (int)groups[pr.gb].members.front();
+    for (size_t g = pr.gb; g < pr.ge; ++g) {
+      const RawGroup &rg = groups[g];
+      GroupDesc d = make_desc(rg, tl, lut);
+      d.m = (uint8_t)rg.members.size();
+      d.rot0 = (uint32_t)(rg.members.front() - pd.rot_begin);
+      P.groups.push_back(d);
+      P.grp_rot_begin.push_back((int)rg.members.front());
+      const uint32_t ncode = 1u << d.r;
+      for (int64_t k : rg.members) {
+        const int ny = popc64(x[k] & z[k]);
+        int sigma = 1;
+        if (rg.kind == KIND_REAL) sigma = (ny % 4 == 1) ? 1 : -1;
+        else if (rg.kind == KIND_XROT) sigma = (ny % 4 == 0) ? 1 : -1;
+        const uint32_t co = rg.basis.coords(z[k]);
+        P.rot_coord[k] = (uint8_t)co;
+        P.rot_sigma[k] = (int8_t)sigma;
+        uint64_t sm = 0;
+        for (uint32_t c = 0; c < ncode; ++c) {
+          const int s = sigma * (parity64(c & co) ? -1 : 1);
+          if (s < 0) sm |= 1ull << c;
+        }
+        P.signmask[k] = sm;
+      }
+      lut += ncode;
+    }
+    pd.g_end = (int)P.groups.size();
+    pd.rot_end = (int)(groups[pr.ge - 1].members.back() + 1);
+    P.max_pass_rots = std::max(P.max_pass_rots, pd.rot_end - pd.rot_begin);
+    P.passes.push_back(pd);
+  }
+  P.lut_entries = lut;
+  return P;
+}
+
+void RotPlan::build_lut(const double *phi, double *lut2) const {
+  for (size_t g = 0; g < groups.size(); ++g) {
+    const GroupDesc &d = groups[g];
+    const uint32_t ncode = 1u << d.r;
+    const int k0 = grp_rot_begin[g];
+    for (uint32_t c = 0; c < ncode; ++c) {
+      double beta = 0.0;
+      for (int k = k0; k < k0 + d.m; ++k) {
+        const double half = 0.5 * phi[k];
+        beta += ((signmask[k] >> c) & 1) ? -half : half;
+      }
+      lut2[2 * (d.lut + c)] = std::cos(beta);
+      lut2[2 * (d.lut + c) + 1] = std::sin(beta);
+    }
+  }
+}
+
+// --------------------------------------------------------------- Hamiltonian
+
+HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z,
+                       const double *c, int Tmax, int Cmin) {
+  HamPlan H;
+  H.n = n;
+  const int T = std::min(Tmax, n);
+  H.T = T;
+  const int C = std::min(Cmin, T);
+  const uint64_t lowmask = (C >= 64) ? ~0ull : ((1ull << C) - 1);
+
+  std::vector<int64_t> order(n_terms);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return x[a] != x[b] ? x[a] < x[b] : z[a] < z[b];
+  });
+
+  // 1. subgroups: same xmask, code rank <= R_MAX
+  std::vector<RawGroup> groups;
+  for (int64_t t : order) {
+    bool join = false;
+    if (!groups.empty()) {
+      RawGroup &g = groups.back();
+      if (g.x == x[t] && (g.basis.contains(z[t]) || g.basis.rank() < R_MAX)) join = true;
+    }
+    if (!join) {
+      groups.emplace_back();
+      groups.back().x = x[t];
+      groups.back().kind = x[t] == 0 ? KIND_DIAG : KIND_PAIR;
+    }
+    groups.back().members.push_back(t);
+    groups.back().basis.add(z[t]);
+  }
+
+  // 2a. groups whose xmask has more qubits than a tile has room for: tiles
+  // spanned by the xmasks themselves (one dimension per independent xmask)
+  std::vector<char> done(groups.size(), 0);
+  size_t remaining = groups.size();
+  std::vector<std::vector<size_t>> pass_groups;
+  std::vector<std::vector<uint64_t>> pass_gens;
+  {
+    Gf2Basis W;
+    std::vector<size_t> cur;
+    std::vector<uint64_t> gens;
+    auto reset = [&]() {
+      W = Gf2Basis();
+      for (int q = 0; q < C; ++q) W.add(1ull << q);
+      cur.clear();
+      gens.clear();
+    };
+    reset();
+    for (size_t g = 0; g < groups.size(); ++g) {
+      if (popc64(groups[g].x | lowmask) <= T) continue;
+      if (!W.contains(groups[g].x) && W.rank() >= T) {
+        pass_groups.push_back(cur);
+        pass_gens.push_back(gens);
+        reset();
+      }
+      if (W.add(groups[g].x)) gens.push_back(groups[g].x);
+      cur.push_back(g);
+      done[g] = 1;
+      --remaining;
+    }
+    if (!cur.empty()) {
+      pass_groups.push_back(cur);
+      pass_gens.push_back(gens);
+    }
+  }
+
+  // 2b. greedy packing of the other subgroups into passes over unit-qubit tiles
+  while (remaining > 0) {
+    uint64_t L = lowmask;
+    std::vector<size_t> chosen;
+    for (;;) {
+      for (size_t g = 0; g < groups.size(); ++g)
+        if (!done[g] && (groups[g].x & ~L) == 0) {
+          done[g] = 1;
+          --remaining;
+          chosen.push_back(g);
+        }
+      if (remaining == 0) break;
+      int freq[64] = {0};
+      for (size_t g = 0; g < groups.size(); ++g)
+        if (!done[g]) {
+          uint64_t v = groups[g].x & ~L;
+          while (v) {
+            ++freq[__builtin_ctzll(v)];
+            v &= v - 1;
+          }
+        }
+      size_t best = groups.size();
+      int best_new = 65;
+      long best_score = -1;
+      for (size_t g = 0; g < groups.size(); ++g) {
+        if (done[g]) continue;
+        const uint64_t nb = groups[g].x & ~L;
+        const int nnew = popc64(nb);
+        if (popc64(L | nb) > T) continue;
+        long score = 0;
+        uint64_t v = nb;
+        while (v) {
+          score += freq[__builtin_ctzll(v)];
+          v &= v - 1;
+        }
+        if (nnew < best_new || (nnew == best_new && score > best_score)) {
+          best = g;
+          best_new = nnew;
+          best_score = score;
+        }
+      }
+      if (best == groups.size()) break;
+      L |= groups[best].x;
+    }
+    if (chosen.empty()) throw std::logic_error("Hamiltonian group does not fit a tile");
+    std::stable_sort(chosen.begin(), chosen.end(), [&](size_t a, size_t b) {
+      return groups[a].kind < groups[b].kind || (groups[a].kind == groups[b].kind && a < b);
+    });
+    pass_groups.push_back(chosen);
+    std::vector<uint64_t> gens;
+    for (int q = 0; q < n; ++q)
+      if ((L >> q) & 1) gens.push_back(1ull << q);
+    pass_gens.push_back(gens);
+  }
+
+  // 3. descriptors and LUT of combined coefficients (R, Q) per code
+  uint32_t lut = 0;
+  for (size_t p = 0; p < pass_groups.size(); ++p) {
+    const Tiling tl = make_tiling(n, T, C, pass_gens[p]);
+    PassDesc pd = make_pass(tl);
+    pd.g_begin = (int)H.groups.size();
+    pd.rot_begin = pd.rot_end = 0;
+    for (size_t g : pass_groups[p]) {
+      const RawGroup &rg = groups[g];
+      GroupDesc d = make_desc(rg, tl, lut);
+      H.groups.push_back(d);
+      const uint32_t ncode = 1u << d.r;
+      H.lut2.resize(2 * (size_t)(lut + ncode), 0.0);
+      for (int64_t t : rg.members) {
+        const int ny = popc64(x[t] & z[t]);
+        const uint32_t co = rg.basis.coords(z[t]);
+        for (uint32_t cd = 0; cd < ncode; ++cd) {
+          const int par = parity64(cd & co);
+          if ((ny & 1) == 0) {
+            const int s = ((ny / 2) + par) & 1;
+            H.lut2[2 * (size_t)(lut + cd)] += s ? -c[t] : c[t];
+          } else {
+            const int s = (par + (ny % 4 == 3)) & 1;
+            H.lut2[2 * (size_t)(lut + cd) + 1] += s ? -c[t] : c[t];
+          }
+        }
+      }
+      lut += ncode;
+    }
+    pd.g_end = (int)H.groups.size();
+    H.passes.push_back(pd);
+  }
+  H.lut_entries = lut;
+  return H;
+}
+
+}  // namespace q2

@@ -1,0 +1,175 @@
+"""CUDA path vs the oracle, element by element, through the C ABI.
+
+Sizes span several tiles and a ragged tail (n = 13 with 12-qubit tiles is
+two tiles; tile sizes are also shrunk to 8 qubits to force many passes at
+small n).  Tolerances: complex128 <= 1e-12 max-abs per amplitude and
+<= 1e-10 Ha in energy (the stated FP64 bar); complex64 <= 1e-5 Ha in energy
+and a per-amplitude bound of 2e-6, derived from FP32 rounding (2^-24 per
+rotation, a few hundred sequential combined rotations per amplitude).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2208_10978_gb300 as q2
+from oracle import statevector as sv
+from oracle import c_oracle
+from synth.workloads import uccsd_energy
+
+pytestmark = pytest.mark.gpu
+
+TOL_AMP = {"complex128": 1e-12, "complex64": 2e-6}
+TOL_E = {"complex128": 1e-10, "complex64": 1e-5}
+
+
+@pytest.fixture(autouse=True)
+def _default_tiles():
+    q2.set_tile_qubits("complex64", 12)
+    q2.set_tile_qubits("complex128", 11)
+    yield
+    q2.set_tile_qubits("complex64", 12)
+    q2.set_tile_qubits("complex128", 11)
+
+
+def to_dev(psi, dtype):
+    return torch.from_numpy(np.asarray(psi, dtype=np.complex128)).to("cuda", getattr(torch, dtype))
+
+
+def to_host(t):
+    torch.cuda.synchronize()
+    return t.to("cpu", torch.complex128).numpy()
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+@pytest.mark.parametrize("n,ne", [(1, 0), (1, 1), (3, 2), (8, 4), (13, 7)])
+def test_init_hf_exact(dtype, n, ne):
+    psi = q2.new_state(n, dtype)
+    psi.fill_(3.0)
+    q2.state_init_hf(psi, n, ne)
+    assert np.array_equal(to_host(psi), sv.hf_state(n, ne))
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_single_rotation_exhaustive(dtype, n):
+    rng = np.random.default_rng(n)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    for x in range(1 << n):
+        for z in range(1 << n):
+            phi = rng.uniform(-3, 3)
+            psi = to_dev(psi0, dtype)
+            q2.apply_pauli_rotations(psi, n, [x], [z], [phi])
+            ref = sv.apply_rotation(psi0, x, z, phi)
+            assert np.max(np.abs(to_host(psi) - ref)) < 4 * TOL_AMP[dtype], (x, z)
+
+
+def _random_rotations(rng, n, k):
+    x = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    x[rng.random(k) < 0.1] = 0
+    z = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    for i in range(1, k):
+        if rng.random() < 0.5:
+            x[i] = x[i - 1]
+    return x, z, rng.uniform(-3, 3, size=k)
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+@pytest.mark.parametrize("n,tile", [(9, 8), (13, None), (16, None), (16, 8), (17, 13)])
+def test_random_rotations_match_oracle(dtype, n, tile):
+    if tile:
+        q2.set_tile_qubits(dtype, tile)
+    rng = np.random.default_rng(10 * n + (tile or 0))
+    x, z, phi = _random_rotations(rng, n, 150)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    psi = to_dev(psi0, dtype)
+    q2.apply_pauli_rotations(psi, n, x, z, phi)
+    ref = c_oracle.apply_rotations(psi0, n, x, z, phi)
+    assert np.max(np.abs(to_host(psi) - ref)) < TOL_AMP[dtype] * (10 if dtype == "complex64" else 1)
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+@pytest.mark.parametrize("n,ne,tile", [(8, 4, None), (12, 6, None), (12, 6, 8), (14, 7, None)])
+def test_uccsd_state_and_energy(dtype, n, ne, tile):
+    if tile:
+        q2.set_tile_qubits(dtype, tile)
+    w = uccsd_energy(n, ne, seed=0)
+    a = w.ansatz
+    psi = q2.new_state(n, dtype)
+    q2.state_init_hf(psi, n, ne)
+    q2.apply_pauli_rotations(psi, n, a.x, a.z, w.angles())
+    ref = c_oracle.apply_rotations(c_oracle.hf_state(n, ne), n, a.x, a.z, w.angles())
+    assert np.max(np.abs(to_host(psi) - ref)) < TOL_AMP[dtype]
+    ham = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
+    e, nrm = ham.expectation(psi)
+    e_ref, n_ref = c_oracle.expectation(ref, n, w.ham.x, w.ham.z, w.ham.c)
+    assert abs(e - e_ref / n_ref) < TOL_E[dtype]
+    assert abs(nrm - 1) < (1e-13 if dtype == "complex128" else 1e-5)
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+@pytest.mark.parametrize("n,tile", [(10, None), (14, None), (14, 8), (3, None)])
+def test_expectation_and_happly_generic(dtype, n, tile):
+    if tile:
+        q2.set_tile_qubits(dtype, tile)
+    rng = np.random.default_rng(300 + n)
+    k = 120
+    x = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    x[:12] = 0
+    x[60:75] = x[60]
+    z = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    c = rng.normal(size=k)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    psi = to_dev(psi0, dtype)
+    ham = q2.Hamiltonian(n, x, z, c)
+    e, nrm = ham.expectation(psi)
+    e_ref, n_ref = c_oracle.expectation(psi0, n, x, z, c)
+    assert abs(e - e_ref / n_ref) < TOL_E[dtype] * 10
+    lam = torch.empty_like(psi)
+    ham.apply(psi, lam)
+    lam_ref = c_oracle.apply_hamiltonian(psi0, n, x, z, c)
+    scale = 1e-11 if dtype == "complex128" else 2e-5
+    assert np.max(np.abs(to_host(lam) - lam_ref)) < scale * max(1.0, np.max(np.abs(lam_ref)))
+
+
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+@pytest.mark.parametrize("n,ne,tile", [(8, 4, None), (10, 4, None), (12, 6, 8)])
+def test_vqe_energy_grad_matches_oracle(dtype, n, ne, tile):
+    if tile:
+        q2.set_tile_qubits(dtype, tile)
+    w = uccsd_energy(n, ne, seed=2)
+    a = w.ansatz
+    ans = q2.Ansatz.from_uccsd(a)
+    ham = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
+    theta = np.random.default_rng(1).normal(0, 0.3, size=a.n_params)
+    e, g, _ = q2.vqe_energy_grad(ans, ham, theta, dtype=dtype, want_grad=True)
+    e0, g0, _ = q2.vqe_energy_grad(ans, ham, theta, dtype=dtype, want_grad=False)
+    e_ref, gphi = c_oracle.energy_and_gradient(n, ne, a.x, a.z, a.angles(theta), w.ham.x, w.ham.z, w.ham.c)
+    g_ref = sv.fold_to_theta(gphi, a.param, a.coef, a.n_params)
+    assert abs(e - e_ref) < TOL_E[dtype]
+    assert abs(e0 - e_ref) < TOL_E[dtype]
+    assert np.max(np.abs(g - g_ref)) < (1e-9 if dtype == "complex128" else 1e-4)
+
+
+def test_autograd_function():
+    w = uccsd_energy(8, 4, seed=3)
+    ans = q2.Ansatz.from_uccsd(w.ansatz)
+    ham = q2.Hamiltonian(8, w.ham.x, w.ham.z, w.ham.c)
+    theta = torch.tensor(w.theta, dtype=torch.float64, requires_grad=True)
+    e = q2.Energy.apply(theta, ans, ham, "complex128")
+    (2.0 * e).backward()
+    a = w.ansatz
+    e_ref, gphi = c_oracle.energy_and_gradient(8, 4, a.x, a.z, a.angles(w.theta), w.ham.x, w.ham.z, w.ham.c)
+    assert abs(e.item() - e_ref) < 1e-10
+    assert np.max(np.abs(theta.grad.numpy() - 2 * sv.fold_to_theta(gphi, a.param, a.coef, a.n_params))) < 2e-9
+
+
+def test_errors_are_loud():
+    psi = q2.new_state(8, "complex64")
+    with pytest.raises(q2.Q2Error):
+        q2.apply_pauli_rotations(psi, 8, [1 << 8], [0], [0.1])
+    with pytest.raises(q2.Q2Error):
+        q2.state_init_hf(psi, 8, 9)

@@ -1,0 +1,205 @@
+"""Host logic of the library, without a GPU.
+
+* libq2.so loads and exports every function declared in include/*.h;
+* argument checks reject bad input before any device work;
+* the pass/group/LUT tables built by the schedulers, walked on the CPU the
+  way the tile kernels index memory (tests/plan_emulator.py), reproduce the
+  oracle's rotations, energies, H|psi> and reverse-mode gradients.
+"""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2208_10978_gb300 as q2
+from oracle import statevector as sv
+from synth import uccsd_rotations
+from synth.workloads import uccsd_energy
+from tests import plan_emulator as emu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return q2.lib()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            txt = re.sub(r"//[^\n]*", "", txt)
+            names |= set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(q2_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 18
+    for nm in sorted(names):
+        assert hasattr(lib, nm), nm
+
+
+def test_version_and_error_text(lib):
+    assert lib.q2_version() >= 100
+    assert isinstance(lib.q2_last_error(), bytes)
+
+
+def _status(f, *args):
+    return f(*args)
+
+
+def test_argument_checks_without_device_work(lib):
+    x = np.array([1 << 9], dtype=np.uint64)
+    z = np.zeros(1, dtype=np.uint64)
+    a = np.array([0.1])
+    P = ctypes.c_void_p
+    dummy = P(256)
+    f = lib.q2_apply_pauli_rotations
+    assert f(dummy, 8, 0, P(x.ctypes.data), P(z.ctypes.data), P(a.ctypes.data), 1, None) == q2.Q2_ERR_INVALID
+    assert b"mask bit" in lib.q2_last_error()
+    assert f(dummy, 0, 0, P(x.ctypes.data), P(z.ctypes.data), P(a.ctypes.data), 1, None) == q2.Q2_ERR_INVALID
+    assert f(dummy, 35, 0, P(x.ctypes.data), P(z.ctypes.data), P(a.ctypes.data), 1, None) == q2.Q2_ERR_INVALID
+    assert f(dummy, 34, 1, P(x.ctypes.data), P(z.ctypes.data), P(a.ctypes.data), 1, None) == q2.Q2_ERR_INVALID
+    bad = np.array([np.nan])
+    xs = np.array([1], dtype=np.uint64)
+    assert f(dummy, 8, 0, P(xs.ctypes.data), P(z.ctypes.data), P(bad.ctypes.data), 1, None) == q2.Q2_ERR_INVALID
+    assert f(P(257), 8, 0, P(xs.ctypes.data), P(z.ctypes.data), P(a.ctypes.data), 1, None) == q2.Q2_ERR_INVALID
+    assert lib.q2_state_init_hf(dummy, 8, 9, 0, None) == q2.Q2_ERR_INVALID
+    assert lib.q2_set_tile_qubits(0, 20) == q2.Q2_ERR_INVALID
+    h = P()
+    c = np.array([np.inf])
+    assert lib.q2_ham_create(8, P(xs.ctypes.data), P(z.ctypes.data), P(c.ctypes.data), 1,
+                             ctypes.byref(h)) == q2.Q2_ERR_INVALID
+    p = np.array([3], dtype=np.int32)
+    one = np.array([1.0])
+    assert lib.q2_ansatz_create(8, 4, 1, P(xs.ctypes.data), P(z.ctypes.data), P(p.ctypes.data),
+                                P(one.ctypes.data), 2, ctypes.byref(h)) == q2.Q2_ERR_INVALID
+
+
+def test_handles_info_without_gpu(lib):
+    w = uccsd_energy(8, 4, seed=0)
+    ham = q2.Hamiltonian(8, w.ham.x, w.ham.z, w.ham.c)
+    assert ham.info() == (361, 51)
+    ans = q2.Ansatz.from_uccsd(w.ansatz)
+    npass, ngroup = ans.info("complex64")
+    assert ngroup == w.ansatz.n_params        # one group per excitation (8 or 2 commuting strings)
+    assert npass >= 1
+    assert ans.workspace_bytes("complex128", True) > 2 * 256 * 16
+
+
+def _random_rotations(rng, n, k, p_zero=0.1):
+    x = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    x[rng.random(k) < p_zero] = 0
+    z = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    # runs of equal x to exercise grouping
+    for i in range(1, k):
+        if rng.random() < 0.5:
+            x[i] = x[i - 1]
+    phi = rng.uniform(-3, 3, size=k)
+    return x, z, phi
+
+
+@pytest.mark.parametrize("n,T,C", [(6, 4, 2), (9, 5, 2), (10, 8, 3), (12, 8, 4), (11, 11, 4), (13, 9, 4)])
+def test_tiles_partition_the_state(lib, n, T, C):
+    rng = np.random.default_rng(n)
+    x, z, phi = _random_rotations(rng, n, 60)
+    passes, groups, lut, sm = emu.rot_plan(lib, n, x, z, phi, T, C)
+    for pd in passes:
+        idx = emu.tile_index(n, pd)
+        assert np.array_equal(np.sort(idx.ravel()), np.arange(1 << n, dtype=np.uint64))
+        for b in range(int(pd["C"])):
+            assert int(pd["w"][b]) == 1 << b
+
+
+@pytest.mark.parametrize("n,T,C,seed", [(6, 4, 2, 0), (9, 5, 2, 1), (10, 8, 3, 2), (12, 8, 4, 3),
+                                        (11, 11, 4, 4), (13, 9, 4, 5), (7, 7, 4, 6)])
+def test_schedule_sweep_matches_oracle(lib, n, T, C, seed):
+    rng = np.random.default_rng(100 + seed)
+    x, z, phi = _random_rotations(rng, n, 120)
+    passes, groups, lut, sm = emu.rot_plan(lib, n, x, z, phi, T, C)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    ref = sv.apply_rotations(psi0, x, z, phi)
+    got = emu.sweep(psi0, n, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    assert np.max(np.abs(got - ref)) < 1e-12
+    back = emu.sweep(got, n, passes, groups, lut, lib.q2_debug_threads_per_cta(), inverse=True)
+    assert np.max(np.abs(back - psi0)) < 1e-12
+
+
+@pytest.mark.parametrize("n,ne,T,C", [(8, 4, 6, 2), (12, 6, 9, 3), (12, 6, 12, 4)])
+def test_schedule_uccsd_matches_oracle(lib, n, ne, T, C):
+    w = uccsd_energy(n, ne, seed=1)
+    a = w.ansatz
+    phi = a.angles(np.random.default_rng(3).normal(0, 0.3, size=a.n_params))
+    passes, groups, lut, sm = emu.rot_plan(lib, n, a.x, a.z, phi, T, C)
+    ref = sv.apply_rotations(sv.hf_state(n, ne), a.x, a.z, phi)
+    got = emu.sweep(sv.hf_state(n, ne), n, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("n,T,C,seed", [(8, 5, 2, 0), (10, 7, 3, 1), (12, 8, 4, 2), (10, 10, 4, 3)])
+def test_schedule_expectation_and_happly(lib, n, T, C, seed):
+    rng = np.random.default_rng(200 + seed)
+    k = 80
+    x = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    x[:10] = 0
+    z = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    c = rng.normal(size=k)
+    x[k // 2:k // 2 + 10] = x[k // 2]            # a group with many terms
+    passes, groups, lut = emu.ham_plan(lib, n, x, z, c, T, C)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    e, nrm = emu.expectation(psi, n, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    assert abs(e - sv.expectation(psi, x, z, c)) < 1e-9 * max(1.0, abs(e))
+    lam = emu.happly(psi, n, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    assert np.max(np.abs(lam - sv.apply_hamiltonian(psi, x, z, c))) < 1e-11
+
+
+def test_schedule_chemistry_hamiltonian(lib):
+    w = uccsd_energy(10, 5, seed=2)
+    passes, groups, lut = emu.ham_plan(lib, 10, w.ham.x, w.ham.z, w.ham.c, 8, 4)
+    psi = sv.apply_rotations(sv.hf_state(10, 5), w.ansatz.x, w.ansatz.z, w.angles())
+    e, nrm = emu.expectation(psi, 10, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    assert abs(e - sv.expectation(psi, w.ham.x, w.ham.z, w.ham.c)) < 1e-11
+
+
+@pytest.mark.parametrize("n,ne,T,C", [(8, 4, 6, 2), (10, 4, 7, 3)])
+def test_schedule_reverse_gradient(lib, n, ne, T, C):
+    w = uccsd_energy(n, ne, seed=4)
+    a = w.ansatz
+    rng = np.random.default_rng(5)
+    phi = a.angles(rng.normal(0, 0.4, size=a.n_params))
+    # add generic rotations (x = 0 groups and even-Y strings) to the tail
+    x2, z2, p2 = _random_rotations(rng, n, 30)
+    X = np.concatenate([a.x, x2])
+    Z = np.concatenate([a.z, z2])
+    PH = np.concatenate([phi, p2])
+    e_ref, g_ref = sv.energy_and_gradient(n, ne, X, Z, PH, w.ham.x, w.ham.z, w.ham.c)
+    NT = lib.q2_debug_threads_per_cta()
+    passes, groups, lut, sm = emu.rot_plan(lib, n, X, Z, PH, T, C)
+    hp, hg, hl = emu.ham_plan(lib, n, w.ham.x, w.ham.z, w.ham.c, T, C)
+    psi = emu.sweep(sv.hf_state(n, ne), n, passes, groups, lut, NT)
+    lam = emu.happly(psi, n, hp, hg, hl, NT)
+    assert abs(np.vdot(psi, lam).real - e_ref) < 1e-11
+    psi_b, lam_b, g = emu.reverse(psi, lam, n, passes, groups, lut, sm, NT)
+    assert np.max(np.abs(g - g_ref)) < 1e-11
+    assert np.max(np.abs(psi_b - sv.hf_state(n, ne))) < 1e-12
+
+
+def test_schedule_fusion_depth_32_qubits(lib):
+    """On the 32-qubit random-order workload, one pass holds many excitations."""
+    from synth import excitations
+    rng = np.random.default_rng(0)
+    pool = excitations(32, 16)
+    chosen = [pool[k] for k in rng.permutation(len(pool))[:200]]
+    a = uccsd_rotations(32, 16, exc_list=chosen)
+    passes, groups, lut, sm = emu.rot_plan(lib, 32, a.x, a.z, np.zeros(a.n_rot), 12, 4)
+    rots_per_pass = a.n_rot / len(passes)
+    assert len(groups) == 200
+    assert rots_per_pass > 40          # one tile dimension per excitation
