@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark: UCCSD Pauli-rotation sweep + grouped energy on one GB300.
+
+Workload (default "sweep32"): 32 qubits, complex64 state (32 GiB), the HF
+determinant of 16 electrons, 50,000 Pauli rotations from randomly ordered
+all-pairs UCCSD excitations, then the energy of a ~30,000-term Hamiltonian
+made of whole xmask groups of the 32-qubit random-integral JW Hamiltonian.
+One step = one q2_vqe_energy_grad call (energy only): HF init, angle
+expansion and LUT upload, every sweep pass, every expectation pass, the
+fixed-order reductions and the read-back of the energy.
+
+metric: amplitude updates per second (rotations x 2^n per step / step time).
+The state (32 GiB) is larger than L2 (129 MB), so no flush is needed.
+
+Flags: --gpus N --steps K --warmup W [--impl ours|reference] [--workload ...]
+Under torchrun (N > 1) every rank runs an independent replica (the sweep
+does not shard); value = all ranks' units / max-over-ranks time.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (n, n_elec, n_rot, min_terms)
+    "sweep32": (32, 16, 50_000, 30_000),
+    "sweep30": (30, 15, 20_000, 10_000),
+    "sweep28": (28, 14, 10_000, 5_000),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev] if vis else dev
+
+
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        import hashlib
+        with open(path) as f:
+            rec = json.load(f)
+        r = rec[kernel]
+        src = os.path.join(ROOT, "paper_2208_10978_gb300", "csrc", "kernels.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if r.get("kernels_cu_sha") != h:
+            return None
+        return r["bytes_per_launch"].get(workload)
+    except Exception:
+        return None
+
+
+def cpu_oracle_sample(n, n_elec, seconds=15.0, seed=0):
+    """Time the plain-C oracle (all host threads) on the first rotations of the
+    random-order UCCSD sweep at n qubits; returns (amp-updates/s, threads, rotations)."""
+    from oracle import c_oracle
+    from synth.workloads import sweep_ansatz
+    ans, theta = sweep_ansatz(n, n_elec, 2000, seed)
+    phi = ans.angles(theta)
+    psi = c_oracle.hf_state(n, n_elec)
+    t = time.perf_counter()
+    psi = c_oracle.apply_rotations(psi, n, ans.x[:2], ans.z[:2], phi[:2])
+    per = (time.perf_counter() - t) / 2
+    k = int(max(2, min(len(phi) - 2, seconds / max(per, 1e-6))))
+    t = time.perf_counter()
+    psi = c_oracle.apply_rotations(psi, n, ans.x[2:2 + k], ans.z[2:2 + k], phi[2:2 + k])
+    dt = time.perf_counter() - t
+    return k * (1 << n) / dt, c_oracle.threads(), k
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the oracle (plain C, host cores) on a bounded sample."""
+    if rank != 0:
+        return 0
+    n_w, ne_w = WORKLOADS[args.workload][:2]
+    n = min(n_w, 28)
+    ne = n // 2
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n, ne, seconds=2.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, k = cpu_oracle_sample(n, ne, seconds=15.0)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    sample = (f"first {k} rotations of the random-order UCCSD sweep at {n} qubits "
+              f"({ne} electrons), complex128 state, plain C oracle")
+    line = {
+        "impl": "reference", "metric": "amp_updates_per_s", "value": value, "unit": "amp-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_qubits": n},
+        "cpu_baseline": {"value": value, "unit": "amp-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "amp-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep32", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import paper_2208_10978_gb300 as q2
+    from synth.workloads import sweep32
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    n, ne, n_rot, min_terms = WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    w = sweep32(seed=0, n=n, n_elec=ne, n_rot=n_rot, min_terms=min_terms)
+    log(f"[bench] workload {args.workload}: {w.ansatz.n_rot} rotations, {w.ham.n_terms} terms "
+        f"({w.ham.n_groups} groups), built in {time.perf_counter() - t0:.1f}s")
+    ans = q2.Ansatz.from_uccsd(w.ansatz)
+    ham = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
+    theta = w.theta
+    lib = q2.lib()
+    import ctypes
+    lib.q2_debug_enable_timing.argtypes = [ctypes.c_int]
+    lib.q2_debug_last_timing.argtypes = [ctypes.c_void_p]
+    lib.q2_debug_enable_timing(1)
+    wsb = ans.workspace_bytes(args.dtype, False)
+    work = q2.alloc_workspace(wsb)
+    tim = np.zeros(8)
+
+    def step():
+        e, _, _ = q2.vqe_energy_grad(ans, ham, theta, dtype=args.dtype, want_grad=False, workspace=work)
+        lib.q2_debug_last_timing(ctypes.c_void_p(tim.ctypes.data))
+        return e, tim.copy()
+
+    for i in range(args.warmup):
+        t = time.perf_counter()
+        e, tt = step()
+        log(f"[bench] warmup {i}: E = {e:.9f}, {time.perf_counter() - t:.2f}s "
+            f"(sweep {tt[0]:.1f} ms / {int(tt[3])} kernels, energy {tt[1]:.1f} ms / {int(tt[4])} kernels)")
+
+    sampler = ClockSampler(gpu_smi_id(torch, local)) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    per = []
+    for _ in range(args.steps):
+        e, tt = step()
+        per.append(tt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tmax = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms = float(tmax.item())
+    per = np.array(per)
+    units_per_step = float(w.ansatz.n_rot) * float(1 << n)
+    value = ws * args.steps * units_per_step / (ms / 1000.0)
+
+    # dominant kernel: the sweep pass (k_sweep), HBM-bound for complex64
+    state_bytes = float(per[0, 7])
+    sweep_ms = float(per[:, 0].mean())
+    sweep_launches = float(per[0, 3])
+    avg_launch_s = sweep_ms / 1000.0 / sweep_launches
+    alg_bytes = 2.0 * state_bytes
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roofline = {"kernel": "k_sweep", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": traffic_record("k_sweep", args.workload),
+                "algorithmic_bytes_per_launch": alg_bytes, "launches_per_step": sweep_launches,
+                "avg_launch_ms": avg_launch_s * 1000.0}
+    expect_ms = float(per[:, 1].mean())
+    gpu_launches = int(per[:, 6].sum())
+
+    e2e = None
+    if not args.no_e2e:
+        # public API from host arrays: table upload, schedule, LUT, energy read-back, every step
+        for _ in range(1):
+            hh = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
+            aa = q2.Ansatz.from_uccsd(w.ansatz)
+            q2.vqe_energy_grad(aa, hh, theta, dtype=args.dtype, want_grad=False, workspace=work)
+            hh.close()
+            aa.close()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            hh = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
+            aa = q2.Ansatz.from_uccsd(w.ansatz)
+            q2.vqe_energy_grad(aa, hh, theta, dtype=args.dtype, want_grad=False, workspace=work)
+            hh.close()
+            aa.close()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t
+        h2d = plan_bytes(lib, w, args.dtype)
+        e2e = {"value": ws * args.steps * units_per_step / wall, "unit": "amp-updates/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        v, cores, k = cpu_oracle_sample(min(n, 28), min(n, 28) // 2, seconds=15.0)
+        cpu = {"value": v, "unit": "amp-updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {k} rotations of the random-order UCCSD sweep at {min(n, 28)} qubits, "
+                         f"complex128, plain C oracle"}
+
+    if rank == 0:
+        line = {
+            "metric": "amp_updates_per_s", "value": value, "unit": "amp-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if args.dtype == "complex64" else "c128", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {n} qubits, {ne} electrons, {w.ansatz.n_rot} UCCSD "
+                                   f"rotations (random excitation order), {w.ham.n_terms}-term JW "
+                                   f"Hamiltonian energy", "state": args.dtype,
+                       "parallelism": f"replicas x{ws}", "l2": "state (2^n amplitudes) larger than L2"},
+            "energy": e,
+            "sweep": {"ms_per_step": sweep_ms, "kernels_per_step": int(sweep_launches),
+                      "amp_updates_per_s": units_per_step / (sweep_ms / 1000.0),
+                      "hbm_gbs": achieved},
+            "expectation": {"ms_per_step": expect_ms, "kernels_per_step": int(per[0, 4]),
+                            "hbm_gbs_read": float(state_bytes * (per[0, 4] - 1) / (expect_ms / 1000.0) / 1e9)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def plan_bytes(lib, w, dtype):
+    """Host->device bytes of one public-API evaluation: Hamiltonian and ansatz
+    tables (group descriptors, LUTs, sign masks) plus the per-call angle LUT."""
+    from tests import plan_emulator as emu
+    amp = 8 if dtype == "complex64" else 16
+    T, C = (12, 4) if dtype == "complex64" else (11, 3)
+    hp, hg, hl = emu.ham_plan(lib, w.n, w.ham.x, w.ham.z, w.ham.c, T, C)
+    rp, rg, rl, sm = emu.rot_plan(lib, w.n, w.ansatz.x, w.ansatz.z, w.angles(), T, C)
+    return int(112 * (len(hg) + len(rg)) + amp * (len(hl) + len(rl)) + 8 * len(sm))
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -8,8 +8,8 @@
  * state vector, not the method.
  *
  * Layouts (little endian, packed as below):
- *   q2_pass   (136 bytes): uint64 w[13] local basis; uint64 umask; int32 T, C,
- *             g_begin, g_end, rot_begin, rot_end.
+ *   q2_pass   (144 bytes): uint64 w[13] local basis; uint64 umask; int32 T, C,
+ *             g_begin, g_end, rot_begin, rot_end, lut_begin, lut_count.
  *   q2_group  (112 bytes): uint64 bp[8] code basis in packed-index space;
  *             uint32 xl, lut, rot0; uint8 kind, pivot, r, m; uint8 jcode[32].
  * counts[0..2] = number of passes, groups, LUT entries.  Output arrays may be
@@ -40,6 +40,19 @@ q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uin
 
 /* Threads per CTA of the tile kernels (the per-thread offsets of q2_group.jcode use it). */
 int q2_debug_threads_per_cta(void);
+
+/*
+ * Per-phase device timing of q2_vqe_energy_grad, for benchmarks.  When
+ * enabled (per calling thread), the call records CUDA events on its own
+ * stream around each phase; q2_debug_last_timing then fills out[0..7] with
+ * the last call's: sweep ms, expectation ms (energy-only) or H-apply + dot ms
+ * (gradient), reverse-sweep ms, number of sweep kernels, number of
+ * expectation / H-apply kernels, number of reverse kernels, total kernels
+ * launched, and the state bytes (2^n * amplitude size).  Returns
+ * Q2_ERR_INVALID if timing was off for the last call.
+ */
+q2_status q2_debug_enable_timing(int enable);
+q2_status q2_debug_last_timing(double *out8);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,30 @@ namespace {
 
 thread_local std::string g_err;
 
+// Per-thread phase timing of q2_vqe_energy_grad (enabled by q2_debug_enable_timing).
+struct PhaseTiming {
+  bool enabled = false;
+  bool valid = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int device = -1;
+  double counts[4] = {0, 0, 0, 0};   // sweep, expect/happly, reverse launches, state bytes
+  double total_launches = 0;
+  bool has_reverse = false;
+  ~PhaseTiming() {}
+  cudaError_t ensure() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (ev[0] && device == dev) return cudaSuccess;
+    for (int i = 0; i < 4; ++i) {
+      if ((e = cudaEventCreate(&ev[i])) != cudaSuccess) return e;
+    }
+    device = dev;
+    return cudaSuccess;
+  }
+};
+thread_local PhaseTiming g_timing;
+
 q2_status fail(q2_status s, const std::string &msg) {
   g_err = msg;
   return s;
@@ -307,24 +331,48 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
   std::vector<unsigned char> lb = lut_bytes(lut2, d);
   Q2_CUDA(cudaMemcpyAsync(base + L.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice, st), "upload LUT");
 
+  const bool timing = g_timing.enabled;
+  g_timing.valid = false;
+  if (timing) Q2_CUDA(g_timing.ensure(), "timing events");
   Q2_CUDA(launch_init_hf<R>(psi, n, a->n_elec, st), "init_hf");
+  if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[0], st), "event");
   Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, base + L.lut, false, st), "sweep");
+  if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[1], st), "event");
   double host_out[2] = {0, 0};
+  g_timing.counts[0] = (double)rp->passes.size();
+  g_timing.counts[3] = (double)((size_t)amp_bytes(d) << n);
   if (!want_grad) {
     const int grid = expect_grid<R>(n, hp->T, std::min(g_chunk[d], hp->T));
     Q2_CUDA(run_expect<R>(psi, n, *hp, *ht, partial, grid, out, st), "expectation");
+    if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[2], st), "event");
     Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
     Q2_CUDA(cudaStreamSynchronize(st), "sync");
     *energy_out = host_out[0] / host_out[1];
+    if (timing) {
+      g_timing.counts[1] = (double)hp->passes.size() + 1;
+      g_timing.counts[2] = 0;
+      g_timing.total_launches = 1 + g_timing.counts[0] + g_timing.counts[1];
+      g_timing.has_reverse = false;
+      g_timing.valid = true;
+    }
     return Q2_OK;
   }
   Q2_CUDA(run_happly<R>(psi, lam, n, *hp, *ht, st), "H apply");
   const int dgrid = dot_grid<R>(n);
   Q2_CUDA(launch_dot<R>(psi, lam, n, partial, dgrid, st), "dot");
   Q2_CUDA(launch_reduce_pairs(partial, dgrid, out, st), "reduce");
+  if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[2], st), "event");
   for (size_t i = rp->passes.size(); i-- > 0;) {
     Q2_CUDA(launch_reverse<R>(psi, lam, n, rp->passes[i], rt->groups, base + L.lut, rt->signmask,
                               partial, gphi, st), "reverse sweep");
+  }
+  if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[3], st), "event");
+  if (timing) {
+    g_timing.counts[1] = (double)hp->passes.size() + 2;
+    g_timing.counts[2] = 2.0 * (double)rp->passes.size();
+    g_timing.total_launches = 1 + g_timing.counts[0] + g_timing.counts[1] + g_timing.counts[2];
+    g_timing.has_reverse = true;
+    g_timing.valid = true;
   }
   std::vector<double> g(nrot);
   Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
@@ -588,7 +636,7 @@ q2_status q2_batch_energy_grad(int n_requests, const q2_ansatz *const *ansatz, c
 
 #include "../../include/q2_debug.h"
 
-static_assert(sizeof(PassDesc) == 136, "q2_pass layout");
+static_assert(sizeof(PassDesc) == 144, "q2_pass layout");
 
 extern "C" {
 
@@ -642,5 +690,29 @@ q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uin
 }
 
 int q2_debug_threads_per_cta(void) { return NT; }
+
+q2_status q2_debug_enable_timing(int enable) {
+  g_timing.enabled = enable != 0;
+  g_timing.valid = false;
+  return Q2_OK;
+}
+
+q2_status q2_debug_last_timing(double *out8) {
+  if (!out8) return fail(Q2_ERR_INVALID, "NULL output");
+  if (!g_timing.valid) return fail(Q2_ERR_INVALID, "no timed call on this thread");
+  float ms[3] = {0, 0, 0};
+  Q2_CUDA(cudaEventElapsedTime(&ms[0], g_timing.ev[0], g_timing.ev[1]), "elapsed");
+  Q2_CUDA(cudaEventElapsedTime(&ms[1], g_timing.ev[1], g_timing.ev[2]), "elapsed");
+  if (g_timing.has_reverse) Q2_CUDA(cudaEventElapsedTime(&ms[2], g_timing.ev[2], g_timing.ev[3]), "elapsed");
+  out8[0] = ms[0];
+  out8[1] = ms[1];
+  out8[2] = ms[2];
+  out8[3] = g_timing.counts[0];
+  out8[4] = g_timing.counts[1];
+  out8[5] = g_timing.counts[2];
+  out8[6] = g_timing.total_launches;
+  out8[7] = g_timing.counts[3];
+  return Q2_OK;
+}
 
 }  // extern "C"

@@ -5,7 +5,13 @@
 // contiguous amplitudes) into shared memory with 16-byte loads, applies all
 // groups of the pass there, and writes the tile back (or only reduces it).
 // Tiles are cosets of the pass's local subspace W (see q2_internal.h), so a
-// pass touches every amplitude exactly once and tiles never overlap.
+// pass touches every amplitude exactly once and tiles never overlap.  The
+// pass's group descriptors and LUT are staged in shared memory once per CTA.
+//
+// Work split inside a tile: pair q = tid + NT*j (j < P) of a group with pivot
+// p is local index insert_zero(q, p) and its partner ^ xl; P = 2^(T-1)/NT is
+// a compile-time constant, so the j loop unrolls and its LUT reads are
+// independent.  Tiles smaller than 2 * NT amplitudes take a guarded P = 1.
 //
 //   k_init_hf     HF determinant (Eq. jw-wfn-map)
 //   k_sweep       rotation groups, forward or inverse (product formula after Eq. ucc)
@@ -46,48 +52,92 @@ __device__ __forceinline__ void st16(V *p, V v) {
   else *p = v;
 }
 
-// Tile geometry shared by all tile kernels.
-struct TileCtx {
-  int T, C;
-  uint32_t tile_amps;     // 2^T
-  uint64_t *off;          // smem: 2^(T-C) chunk offsets
+// ------------------------------------------------------------------ shared-memory layout
+
+// [tiles: vectors * 2^T amplitudes][off: 2^(T-C) u64][groups][lut][extra]
+struct SmemLayout {
+  size_t tiles, off, groups, lut, extra, total;
 };
 
-__device__ __forceinline__ void build_offsets(const PassDesc &pd, uint64_t *off) {
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+__host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc &pd, int vectors,
+                                                  size_t extra_bytes) {
+  SmemLayout L;
+  size_t o = 0;
+  L.tiles = o;
+  o = align16(o + (size_t)amp_bytes * ((size_t)1 << pd.T) * vectors);
+  L.off = o;
+  o = align16(o + sizeof(uint64_t) * ((size_t)1 << (pd.T - pd.C)));
+  L.groups = o;
+  o = align16(o + sizeof(GroupDesc) * (size_t)(pd.g_end - pd.g_begin));
+  L.lut = o;
+  o = align16(o + (size_t)amp_bytes * (size_t)pd.lut_count);
+  L.extra = o;
+  o = align16(o + extra_bytes);
+  L.total = o;
+  return L;
+}
+
+template <typename R> struct Tile {
+  using C2 = typename Vec2<R>::type;
+  int T, C;
+  uint32_t amps;
+  uint64_t *off;
+  const GroupDesc *gs;   // staged groups of the pass (index g - g_begin)
+  const C2 *lut;         // staged LUT (index lut - lut_begin)
+};
+
+// Stage offsets, group descriptors and LUT of a pass; caller syncs.
+template <typename R>
+__device__ __forceinline__ Tile<R> stage_pass(unsigned char *smem, const PassDesc &pd,
+                                              const SmemLayout &L, const GroupDesc *groups,
+                                              const typename Vec2<R>::type *lut) {
+  using C2 = typename Vec2<R>::type;
+  Tile<R> t;
+  t.T = pd.T;
+  t.C = pd.C;
+  t.amps = 1u << pd.T;
+  t.off = reinterpret_cast<uint64_t *>(smem + L.off);
   const int nh = 1 << (pd.T - pd.C);
-  for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+  for (int h = threadIdx.x; h < nh; h += NT) {
     uint64_t o = 0;
     for (int b = 0; b < pd.T - pd.C; ++b)
       if ((h >> b) & 1) o ^= pd.w[pd.C + b];
-    off[h] = o;
+    t.off[h] = o;
   }
+  const int ng = pd.g_end - pd.g_begin;
+  uint4 *gd = reinterpret_cast<uint4 *>(smem + L.groups);
+  const uint4 *gsrc = reinterpret_cast<const uint4 *>(groups + pd.g_begin);
+  for (int i = threadIdx.x; i < ng * (int)(sizeof(GroupDesc) / 16); i += NT) gd[i] = __ldg(gsrc + i);
+  C2 *ld = reinterpret_cast<C2 *>(smem + L.lut);
+  for (int i = threadIdx.x; i < pd.lut_count; i += NT) ld[i] = __ldg(lut + pd.lut_begin + i);
+  t.gs = reinterpret_cast<const GroupDesc *>(smem + L.groups);
+  t.lut = ld - pd.lut_begin;
+  return t;
 }
 
-__device__ __forceinline__ uint64_t tile_base(uint64_t t, uint64_t umask) {
-  return deposit_bits(t, umask);
-}
-
-// Amplitude index of vector v (16-byte unit) of a tile.
-template <typename R>
-__device__ __forceinline__ uint64_t vec_index(uint64_t base, uint32_t v, const TileCtx &tc) {
-  const uint32_t l = v * Vec16<R>::amps;
-  const uint32_t cm = (1u << tc.C) - 1u;
-  return (base ^ tc.off[l >> tc.C]) | (l & cm);
-}
+__device__ __forceinline__ uint64_t tile_base(uint64_t t, uint64_t umask) { return deposit_bits(t, umask); }
 
 // Gather one tile of `src` into shared memory.
 template <typename R, bool STREAM>
-__device__ __forceinline__ void load_tile(const R *src, uint64_t base, const TileCtx &tc,
+__device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Tile<R> &tc,
                                           typename Vec16<R>::type *dst) {
   using V = typename Vec16<R>::type;
-  const uint32_t nv = tc.tile_amps / Vec16<R>::amps;
+  constexpr int A = Vec16<R>::amps;
+  const uint32_t nv = tc.amps / A;
+  const uint32_t cm = (1u << tc.C) - 1u;
   const V *g = reinterpret_cast<const V *>(src);
   for (uint32_t v0 = 0; v0 < nv; v0 += 8 * NT) {
     V buf[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const uint32_t v = v0 + k * NT + threadIdx.x;
-      if (v < nv) buf[k] = ld16<V, STREAM>(g + vec_index<R>(base, v, tc) / Vec16<R>::amps);
+      if (v < nv) {
+        const uint32_t l = v * A;
+        const uint64_t i = (base ^ tc.off[l >> tc.C]) | (l & cm);
+        buf[k] = ld16<V, STREAM>(g + i / A);
+      }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -98,25 +148,38 @@ __device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Til
 }
 
 template <typename R, bool STREAM>
-__device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const TileCtx &tc,
+__device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Tile<R> &tc,
                                            const typename Vec16<R>::type *src) {
   using V = typename Vec16<R>::type;
-  const uint32_t nv = tc.tile_amps / Vec16<R>::amps;
+  constexpr int A = Vec16<R>::amps;
+  const uint32_t nv = tc.amps / A;
+  const uint32_t cm = (1u << tc.C) - 1u;
   V *g = reinterpret_cast<V *>(dstg);
-  for (uint32_t v = threadIdx.x; v < nv; v += NT)
-    st16<V, STREAM>(g + vec_index<R>(base, v, tc) / Vec16<R>::amps, src[v]);
+#pragma unroll 4
+  for (uint32_t v = threadIdx.x; v < nv; v += NT) {
+    const uint32_t l = v * A;
+    const uint64_t i = (base ^ tc.off[l >> tc.C]) | (l & cm);
+    st16<V, STREAM>(g + i / A, src[v]);
+  }
 }
 
 // Code of the thread's first element of a group in the current tile.
-__device__ __forceinline__ uint32_t thread_code(const GroupDesc *gd, int r, uint64_t packed) {
+__device__ __forceinline__ uint32_t thread_code(const GroupDesc &d, int r, uint64_t packed) {
   uint32_t code = 0;
-  for (int l = 0; l < r; ++l) code |= (uint32_t)par64(packed & __ldg(&gd->bp[l])) << l;
+  for (int l = 0; l < r; ++l) code |= (uint32_t)par64(packed & d.bp[l]) << l;
   return code;
 }
 
-__device__ __forceinline__ uint32_t jcode_of(const GroupDesc *gd, int j) {
-  return __ldg(&gd->jcode[j]);
-}
+// Work assignment of one group for a thread: local indices of its P pairs
+// (or 2P diagonal amplitudes) and their codes.
+template <int P, bool GUARD>
+struct PairIter {
+  uint32_t li0, code0;
+  int pivot;
+  __device__ __forceinline__ uint32_t li(int j) const {
+    return li0 | insert_zero((uint32_t)(NT * j), pivot);
+  }
+};
 
 // ------------------------------------------------------------------ init
 
@@ -138,53 +201,48 @@ __global__ void k_init_hf(R *psi, uint64_t n_amps, uint64_t hf) {
 
 // ------------------------------------------------------------------ rotation sweep
 
-// Apply rotation group gd (sign +1 forward, -1 inverse) to a shared-memory tile.
-template <typename R>
-__device__ __forceinline__ void rot_group(typename Vec2<R>::type *tile, const GroupDesc *gd,
-                                          const typename Vec2<R>::type *lut, uint64_t tpacked,
-                                          int T, R sgn) {
+// Apply one rotation group (sign +1 forward, -1 inverse) to a shared-memory tile.
+template <typename R, int P, bool GUARD>
+__device__ __forceinline__ void rot_group(typename Vec2<R>::type *tile, const GroupDesc &d,
+                                          const Tile<R> &tc, uint64_t tpacked, R sgn) {
   using C2 = typename Vec2<R>::type;
-  const int kind = __ldg(&gd->kind);
-  const int r = __ldg(&gd->r);
-  const uint32_t lut0 = __ldg(&gd->lut);
+  const int kind = d.kind;
+  const int r = d.r;
+  const C2 *lut = tc.lut + d.lut;
+  const uint32_t tid = threadIdx.x;
   if (kind == KIND_DIAG) {
-    const uint32_t n_amp = 1u << T;
-    const int P = n_amp > NT ? (int)(n_amp / NT) : 1;
-    const uint32_t code0 = thread_code(gd, r, tpacked | threadIdx.x);
-    for (int j = 0; j < P; ++j) {
-      const uint32_t l = threadIdx.x + NT * j;
-      if (l >= n_amp) break;
-      const C2 cs = __ldg(&lut[lut0 + (code0 ^ jcode_of(gd, j))]);
+    const uint32_t code0 = thread_code(d, r, tpacked | tid);
+#pragma unroll
+    for (int j = 0; j < 2 * P; ++j) {
+      const uint32_t l = tid + NT * j;
+      if (GUARD && l >= tc.amps) break;
+      const C2 cs = lut[code0 ^ d.jcode[j]];
       const R c = cs.x, s = sgn * cs.y;
       const C2 a = tile[l];
       tile[l] = C2{c * a.x + s * a.y, c * a.y - s * a.x};
     }
     return;
   }
-  const int pivot = __ldg(&gd->pivot);
-  const uint32_t xl = __ldg(&gd->xl);
-  const uint32_t n_pair = 1u << (T - 1);
-  const int P = n_pair > NT ? (int)(n_pair / NT) : 1;
-  const uint32_t code0 = thread_code(gd, r, tpacked | insert_zero(threadIdx.x, pivot));
+  const int pivot = d.pivot;
+  const uint32_t xl = d.xl;
+  if (GUARD && tid >= (tc.amps >> 1)) return;
+  const uint32_t li0 = insert_zero(tid, pivot);
+  const uint32_t code0 = thread_code(d, r, tpacked | li0);
   if (kind == KIND_REAL) {
-#pragma unroll 4
+#pragma unroll
     for (int j = 0; j < P; ++j) {
-      const uint32_t q = threadIdx.x + NT * j;
-      if (q >= n_pair) break;
-      const uint32_t li = insert_zero(q, pivot), lj = li ^ xl;
-      const C2 cs = __ldg(&lut[lut0 + (code0 ^ jcode_of(gd, j))]);
+      const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
+      const C2 cs = lut[code0 ^ d.jcode[j]];
       const R c = cs.x, s = sgn * cs.y;
       const C2 a = tile[li], b = tile[lj];
       tile[li] = C2{c * a.x - s * b.x, c * a.y - s * b.y};
       tile[lj] = C2{s * a.x + c * b.x, s * a.y + c * b.y};
     }
   } else {
-#pragma unroll 4
+#pragma unroll
     for (int j = 0; j < P; ++j) {
-      const uint32_t q = threadIdx.x + NT * j;
-      if (q >= n_pair) break;
-      const uint32_t li = insert_zero(q, pivot), lj = li ^ xl;
-      const C2 cs = __ldg(&lut[lut0 + (code0 ^ jcode_of(gd, j))]);
+      const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
+      const C2 cs = lut[code0 ^ d.jcode[j]];
       const R c = cs.x, s = sgn * cs.y;
       const C2 a = tile[li], b = tile[lj];
       tile[li] = C2{c * a.x + s * b.y, c * a.y - s * b.x};
@@ -193,37 +251,28 @@ __device__ __forceinline__ void rot_group(typename Vec2<R>::type *tile, const Gr
   }
 }
 
-template <typename R, bool STREAM>
-__global__ void __launch_bounds__(NT) k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups,
-                                              const typename Vec2<R>::type *lut, int inverse) {
+template <typename R, bool STREAM, int P, bool GUARD>
+__global__ void __launch_bounds__(NT, 4) k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups,
+                                                 const typename Vec2<R>::type *lut, int inverse) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  TileCtx tc;
-  tc.T = pd.T;
-  tc.C = pd.C;
-  tc.tile_amps = 1u << pd.T;
-  C2 *tile = reinterpret_cast<C2 *>(smem);
-  tc.off = reinterpret_cast<uint64_t *>(smem + sizeof(C2) * tc.tile_amps);
-  build_offsets(pd, tc.off);
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, 0);
+  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+  C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   const R sgn = inverse ? (R)-1 : (R)1;
+  const int ng = pd.g_end - pd.g_begin;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
     load_tile<R, STREAM>(psi, base, tc, reinterpret_cast<V *>(tile));
     __syncthreads();
     const uint64_t tpacked = t << pd.T;
-    if (!inverse) {
-      for (int g = pd.g_begin; g < pd.g_end; ++g) {
-        rot_group<R>(tile, groups + g, lut, tpacked, pd.T, sgn);
-        __syncthreads();
-      }
-    } else {
-      for (int g = pd.g_end - 1; g >= pd.g_begin; --g) {
-        rot_group<R>(tile, groups + g, lut, tpacked, pd.T, sgn);
-        __syncthreads();
-      }
+    for (int k = 0; k < ng; ++k) {
+      const int g = inverse ? ng - 1 - k : k;
+      rot_group<R, P, GUARD>(tile, tc.gs[g], tc, tpacked, sgn);
+      __syncthreads();
     }
     store_tile<R, STREAM>(psi, base, tc, reinterpret_cast<const V *>(tile));
     __syncthreads();
@@ -259,26 +308,23 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 
 // ------------------------------------------------------------------ expectation
 
-template <typename R, bool STREAM>
-__global__ void __launch_bounds__(NT) k_expect(const R *psi, int n, PassDesc pd,
-                                               const GroupDesc *groups,
-                                               const typename Vec2<R>::type *lut, double *partial,
-                                               int first_pass) {
+template <typename R, bool STREAM, int P, bool GUARD>
+__global__ void __launch_bounds__(NT, 4) k_expect(const R *psi, int n, PassDesc pd,
+                                                  const GroupDesc *groups,
+                                                  const typename Vec2<R>::type *lut, double *partial,
+                                                  int first_pass) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  TileCtx tc;
-  tc.T = pd.T;
-  tc.C = pd.C;
-  tc.tile_amps = 1u << pd.T;
-  C2 *tile = reinterpret_cast<C2 *>(smem);
-  tc.off = reinterpret_cast<uint64_t *>(smem + sizeof(C2) * tc.tile_amps);
-  double *red = reinterpret_cast<double *>(tc.off + (1u << (pd.T - pd.C)));
-  build_offsets(pd, tc.off);
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32));
+  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+  C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
+  double *red = reinterpret_cast<double *>(smem + L.extra);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
+  const int ng = pd.g_end - pd.g_begin;
+  const uint32_t tid = threadIdx.x;
   Kahan<R> acc_e, acc_n;
-  const uint32_t n_amp = tc.tile_amps, n_pair = n_amp >> 1;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
     load_tile<R, STREAM>(psi, base, tc, reinterpret_cast<V *>(tile));
@@ -286,44 +332,46 @@ __global__ void __launch_bounds__(NT) k_expect(const R *psi, int n, PassDesc pd,
     const uint64_t tpacked = t << pd.T;
     if (first_pass) {
       R s = 0;
-      for (uint32_t l = threadIdx.x; l < n_amp; l += NT) {
+#pragma unroll
+      for (int j = 0; j < 2 * P; ++j) {
+        const uint32_t l = tid + NT * j;
+        if (GUARD && l >= tc.amps) break;
         const C2 a = tile[l];
         s += a.x * a.x + a.y * a.y;
       }
       acc_n.add(s);
     }
-    for (int g = pd.g_begin; g < pd.g_end; ++g) {
-      const GroupDesc *gd = groups + g;
-      const int kind = __ldg(&gd->kind), r = __ldg(&gd->r);
-      const uint32_t lut0 = __ldg(&gd->lut);
+    for (int k = 0; k < ng; ++k) {
+      const GroupDesc &d = tc.gs[k];
+      const C2 *lt = tc.lut + d.lut;
+      const int r = d.r;
       R s = 0;
-      if (kind == KIND_DIAG) {
-        const int P = n_amp > NT ? (int)(n_amp / NT) : 1;
-        const uint32_t code0 = thread_code(gd, r, tpacked | threadIdx.x);
-        for (int j = 0; j < P; ++j) {
-          const uint32_t l = threadIdx.x + NT * j;
-          if (l >= n_amp) break;
-          const R d = __ldg(&lut[lut0 + (code0 ^ jcode_of(gd, j))]).x;
+      if (d.kind == KIND_DIAG) {
+        const uint32_t code0 = thread_code(d, r, tpacked | tid);
+#pragma unroll
+        for (int j = 0; j < 2 * P; ++j) {
+          const uint32_t l = tid + NT * j;
+          if (GUARD && l >= tc.amps) break;
+          const R dv = lt[code0 ^ d.jcode[j]].x;
           const C2 a = tile[l];
-          s += d * (a.x * a.x + a.y * a.y);
+          s += dv * (a.x * a.x + a.y * a.y);
         }
-      } else {
-        const int pivot = __ldg(&gd->pivot);
-        const uint32_t xl = __ldg(&gd->xl);
-        const int P = n_pair > NT ? (int)(n_pair / NT) : 1;
-        const uint32_t code0 = thread_code(gd, r, tpacked | insert_zero(threadIdx.x, pivot));
-#pragma unroll 4
+      } else if (!GUARD || tid < (tc.amps >> 1)) {
+        const int pivot = d.pivot;
+        const uint32_t xl = d.xl;
+        const uint32_t li0 = insert_zero(tid, pivot);
+        const uint32_t code0 = thread_code(d, r, tpacked | li0);
+#pragma unroll
         for (int j = 0; j < P; ++j) {
-          const uint32_t q = threadIdx.x + NT * j;
-          if (q >= n_pair) break;
-          const uint32_t li = insert_zero(q, pivot), lj = li ^ xl;
-          const C2 rq = __ldg(&lut[lut0 + (code0 ^ jcode_of(gd, j))]);
+          const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
+          const C2 rq = lt[code0 ^ d.jcode[j]];
           const C2 a = tile[li], b = tile[lj];
           // w = conj(a) b ; contribution 2 (R Re w + Q Im w)
           const R wr = a.x * b.x + a.y * b.y;
           const R wi = a.x * b.y - a.y * b.x;
-          s += 2 * (rq.x * wr + rq.y * wi);
+          s += rq.x * wr + rq.y * wi;
         }
+        s *= 2;
       }
       acc_e.add(s);
     }
@@ -367,62 +415,57 @@ __global__ void k_reduce_pairs(const double *partial, int nblocks, double *out) 
 
 // ------------------------------------------------------------------ H apply
 
-template <typename R, bool STREAM>
-__global__ void __launch_bounds__(NT) k_happly(const R *psi, R *lam, int n, PassDesc pd,
-                                               const GroupDesc *groups,
-                                               const typename Vec2<R>::type *lut, int first_pass) {
+template <typename R, bool STREAM, int P, bool GUARD>
+__global__ void __launch_bounds__(NT, 3) k_happly(const R *psi, R *lam, int n, PassDesc pd,
+                                                  const GroupDesc *groups,
+                                                  const typename Vec2<R>::type *lut, int first_pass) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  TileCtx tc;
-  tc.T = pd.T;
-  tc.C = pd.C;
-  tc.tile_amps = 1u << pd.T;
-  C2 *tp = reinterpret_cast<C2 *>(smem);
-  C2 *tl = tp + tc.tile_amps;
-  tc.off = reinterpret_cast<uint64_t *>(tl + tc.tile_amps);
-  build_offsets(pd, tc.off);
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 2, 0);
+  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+  C2 *tp = reinterpret_cast<C2 *>(smem + L.tiles);
+  C2 *tl = tp + tc.amps;
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
-  const uint32_t n_amp = tc.tile_amps, n_pair = n_amp >> 1;
+  const int ng = pd.g_end - pd.g_begin;
+  const uint32_t tid = threadIdx.x;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
     load_tile<R, STREAM>(psi, base, tc, reinterpret_cast<V *>(tp));
     if (first_pass) {
-      for (uint32_t l = threadIdx.x; l < n_amp; l += NT) tl[l] = C2{0, 0};
+      for (uint32_t l = tid; l < tc.amps; l += NT) tl[l] = C2{0, 0};
     } else {
       load_tile<R, STREAM>(lam, base, tc, reinterpret_cast<V *>(tl));
     }
     __syncthreads();
     const uint64_t tpacked = t << pd.T;
-    for (int g = pd.g_begin; g < pd.g_end; ++g) {
-      const GroupDesc *gd = groups + g;
-      const int kind = __ldg(&gd->kind), r = __ldg(&gd->r);
-      const uint32_t lut0 = __ldg(&gd->lut);
-      if (kind == KIND_DIAG) {
-        const int P = n_amp > NT ? (int)(n_amp / NT) : 1;
-        const uint32_t code0 = thread_code(gd, r, tpacked | threadIdx.x);
-        for (int j = 0; j < P; ++j) {
-          const uint32_t l = threadIdx.x + NT * j;
-          if (l >= n_amp) break;
-          const R d = __ldg(&lut[lut0 + (code0 ^ jcode_of(gd, j))]).x;
+    for (int k = 0; k < ng; ++k) {
+      const GroupDesc &d = tc.gs[k];
+      const C2 *lt = tc.lut + d.lut;
+      const int r = d.r;
+      if (d.kind == KIND_DIAG) {
+        const uint32_t code0 = thread_code(d, r, tpacked | tid);
+#pragma unroll
+        for (int j = 0; j < 2 * P; ++j) {
+          const uint32_t l = tid + NT * j;
+          if (GUARD && l >= tc.amps) break;
+          const R dv = lt[code0 ^ d.jcode[j]].x;
           const C2 a = tp[l];
           C2 o = tl[l];
-          o.x += d * a.x;
-          o.y += d * a.y;
+          o.x += dv * a.x;
+          o.y += dv * a.y;
           tl[l] = o;
         }
-      } else {
-        const int pivot = __ldg(&gd->pivot);
-        const uint32_t xl = __ldg(&gd->xl);
-        const int P = n_pair > NT ? (int)(n_pair / NT) : 1;
-        const uint32_t code0 = thread_code(gd, r, tpacked | insert_zero(threadIdx.x, pivot));
-#pragma unroll 4
+      } else if (!GUARD || tid < (tc.amps >> 1)) {
+        const int pivot = d.pivot;
+        const uint32_t xl = d.xl;
+        const uint32_t li0 = insert_zero(tid, pivot);
+        const uint32_t code0 = thread_code(d, r, tpacked | li0);
+#pragma unroll
         for (int j = 0; j < P; ++j) {
-          const uint32_t q = threadIdx.x + NT * j;
-          if (q >= n_pair) break;
-          const uint32_t li = insert_zero(q, pivot), lj = li ^ xl;
-          const C2 rq = __ldg(&lut[lut0 + (code0 ^ jcode_of(gd, j))]);
+          const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
+          const C2 rq = lt[code0 ^ d.jcode[j]];
           const C2 a = tp[li], b = tp[lj];
           C2 oi = tl[li], oj = tl[lj];
           // lam_i += (R - iQ) psi_j ; lam_j += (R + iQ) psi_i
@@ -475,29 +518,27 @@ __global__ void __launch_bounds__(NT) k_dot(const R *psi, const R *lam, uint64_t
 
 // ------------------------------------------------------------------ reverse sweep
 
-template <typename R, bool STREAM>
-__global__ void __launch_bounds__(NT) k_reverse(R *psi, R *lam, int n, PassDesc pd,
-                                                const GroupDesc *groups,
-                                                const typename Vec2<R>::type *lut,
-                                                const uint64_t *signmask, double *partial) {
+template <typename R, bool STREAM, int P, bool GUARD>
+__global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDesc pd,
+                                                   const GroupDesc *groups,
+                                                   const typename Vec2<R>::type *lut,
+                                                   const uint64_t *signmask, double *partial) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  TileCtx tc;
-  tc.T = pd.T;
-  tc.C = pd.C;
-  tc.tile_amps = 1u << pd.T;
-  C2 *tp = reinterpret_cast<C2 *>(smem);
-  C2 *tl = tp + tc.tile_amps;
-  tc.off = reinterpret_cast<uint64_t *>(tl + tc.tile_amps);
-  double *acc = reinterpret_cast<double *>(tc.off + (1u << (pd.T - pd.C)));  // [RP_MAX]
-  R *wpart = reinterpret_cast<R *>(acc + RP_MAX);                              // [NT/32][M_MAX]
-  build_offsets(pd, tc.off);
+  const SmemLayout L =
+      smem_layout(sizeof(C2), pd, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX);
+  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+  C2 *tp = reinterpret_cast<C2 *>(smem + L.tiles);
+  C2 *tl = tp + tc.amps;
+  double *acc = reinterpret_cast<double *>(smem + L.extra);   // [RP_MAX]
+  R *wpart = reinterpret_cast<R *>(acc + RP_MAX);             // [NT/32][M_MAX]
   const int nrot = pd.rot_end - pd.rot_begin;
   for (int k = threadIdx.x; k < nrot; k += NT) acc[k] = 0.0;
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
-  const uint32_t n_amp = tc.tile_amps, n_pair = n_amp >> 1;
+  const int ng = pd.g_end - pd.g_begin;
+  const uint32_t tid = threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
@@ -505,47 +546,46 @@ __global__ void __launch_bounds__(NT) k_reverse(R *psi, R *lam, int n, PassDesc 
     load_tile<R, STREAM>(lam, base, tc, reinterpret_cast<V *>(tl));
     __syncthreads();
     const uint64_t tpacked = t << pd.T;
-    for (int g = pd.g_end - 1; g >= pd.g_begin; --g) {
-      const GroupDesc *gd = groups + g;
-      const int kind = __ldg(&gd->kind), r = __ldg(&gd->r), m = __ldg(&gd->m);
-      const uint32_t lut0 = __ldg(&gd->lut);
-      const int rot0 = (int)__ldg(&gd->rot0);
+    for (int k = ng - 1; k >= 0; --k) {
+      const GroupDesc &d = tc.gs[k];
+      const C2 *lt = tc.lut + d.lut;
+      const int kind = d.kind, r = d.r, m = d.m;
+      const int rot0 = (int)d.rot0;
       const uint64_t *sm = signmask + pd.rot_begin + rot0;
       uint64_t mask[M_MAX];
       R a_k[M_MAX];
 #pragma unroll
-      for (int k = 0; k < M_MAX; ++k) {
-        mask[k] = k < m ? __ldg(&sm[k]) : 0ull;
-        a_k[k] = 0;
+      for (int q = 0; q < M_MAX; ++q) {
+        mask[q] = q < m ? __ldg(&sm[q]) : 0ull;
+        a_k[q] = 0;
       }
       if (kind == KIND_DIAG) {
-        const int P = n_amp > NT ? (int)(n_amp / NT) : 1;
-        const uint32_t code0 = thread_code(gd, r, tpacked | threadIdx.x);
-        for (int j = 0; j < P; ++j) {
-          const uint32_t l = threadIdx.x + NT * j;
-          if (l >= n_amp) break;
-          const uint32_t code = code0 ^ jcode_of(gd, j);
-          const C2 cs = __ldg(&lut[lut0 + code]);
+        const uint32_t code0 = thread_code(d, r, tpacked | tid);
+#pragma unroll
+        for (int j = 0; j < 2 * P; ++j) {
+          const uint32_t l = tid + NT * j;
+          if (GUARD && l >= tc.amps) break;
+          const uint32_t code = code0 ^ d.jcode[j];
+          const C2 cs = lt[code];
           const C2 a = tp[l], b = tl[l];
           const R val = b.x * a.y - b.y * a.x;   // Im(conj(lam) psi)
 #pragma unroll
-          for (int k = 0; k < M_MAX; ++k)
-            if (k < m) a_k[k] += ((mask[k] >> code) & 1) ? -val : val;
+          for (int q = 0; q < M_MAX; ++q)
+            if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
           const R c = cs.x, s = -cs.y;
           tp[l] = C2{c * a.x + s * a.y, c * a.y - s * a.x};
           tl[l] = C2{c * b.x + s * b.y, c * b.y - s * b.x};
         }
-      } else {
-        const int pivot = __ldg(&gd->pivot);
-        const uint32_t xl = __ldg(&gd->xl);
-        const int P = n_pair > NT ? (int)(n_pair / NT) : 1;
-        const uint32_t code0 = thread_code(gd, r, tpacked | insert_zero(threadIdx.x, pivot));
+      } else if (!GUARD || tid < (tc.amps >> 1)) {
+        const int pivot = d.pivot;
+        const uint32_t xl = d.xl;
+        const uint32_t li0 = insert_zero(tid, pivot);
+        const uint32_t code0 = thread_code(d, r, tpacked | li0);
+#pragma unroll
         for (int j = 0; j < P; ++j) {
-          const uint32_t q = threadIdx.x + NT * j;
-          if (q >= n_pair) break;
-          const uint32_t li = insert_zero(q, pivot), lj = li ^ xl;
-          const uint32_t code = code0 ^ jcode_of(gd, j);
-          const C2 cs = __ldg(&lut[lut0 + code]);
+          const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
+          const uint32_t code = code0 ^ d.jcode[j];
+          const C2 cs = lt[code];
           const C2 pa = tp[li], pb = tp[lj], la = tl[li], lb = tl[lj];
           R val;
           if (kind == KIND_REAL) {
@@ -556,8 +596,8 @@ __global__ void __launch_bounds__(NT) k_reverse(R *psi, R *lam, int n, PassDesc 
             val = (la.x * pb.y - la.y * pb.x) + (lb.x * pa.y - lb.y * pa.x);
           }
 #pragma unroll
-          for (int k = 0; k < M_MAX; ++k)
-            if (k < m) a_k[k] += ((mask[k] >> code) & 1) ? -val : val;
+          for (int q = 0; q < M_MAX; ++q)
+            if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
           const R c = cs.x, s = -cs.y;
           if (kind == KIND_REAL) {
             tp[li] = C2{c * pa.x - s * pb.x, c * pa.y - s * pb.y};
@@ -574,11 +614,11 @@ __global__ void __launch_bounds__(NT) k_reverse(R *psi, R *lam, int n, PassDesc 
       }
       // warp sums -> smem -> fixed-order CTA sum into acc (double)
 #pragma unroll
-      for (int k = 0; k < M_MAX; ++k) {
-        if (k < m) {
-          R v = a_k[k];
+      for (int q = 0; q < M_MAX; ++q) {
+        if (q < m) {
+          R v = a_k[q];
           for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0) wpart[warp * M_MAX + k] = v;
+          if (lane == 0) wpart[warp * M_MAX + q] = v;
         }
       }
       __syncthreads();
@@ -609,18 +649,10 @@ __global__ void k_reduce_rot(const double *partial, int nblocks, int nrot, doubl
 
 namespace {
 
-template <typename K>
-int blocks_per_sm(K kernel, size_t smem) {
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, NT, smem) != cudaSuccess) return 1;
-  return b > 0 ? b : 1;
-}
-
 int sm_count() {
-  static int cached = -1;
+  static int cached = -1, cached_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
-  static int cached_dev = -1;
   if (cached < 0 || cached_dev != dev) {
     cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
     cached_dev = dev;
@@ -629,32 +661,65 @@ int sm_count() {
 }
 
 template <typename K>
-cudaError_t set_smem(K kernel, size_t smem) {
+int blocks_per_sm(K kernel, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, NT, smem) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
+template <typename K>
+cudaError_t prepare(K kernel, size_t smem) {
   if (smem > 48 * 1024)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaSuccess;
 }
 
-uint64_t grid_for(uint64_t ntiles, int per_sm) {
+unsigned grid_for(uint64_t ntiles, int per_sm) {
   const uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
-  return ntiles < cap ? ntiles : cap;
+  return (unsigned)(ntiles < cap ? ntiles : cap);
 }
+
+bool streaming(int n, int bytes) { return ((uint64_t)bytes << n) > (64ull << 20); }
+
+// Pick the kernel instantiation for a pass: P = 2^(T-1) / NT pairs per thread.
+#define Q2_DISPATCH(KERNEL, R, n, T, ...)                                              \
+  [&]() -> decltype(&KERNEL<R, true, 1, true>) {                                     \
+    const bool st_ = streaming(n, 2 * (int)sizeof(R));                               \
+    switch (T) {                                                                       \
+      case 9: return st_ ? &KERNEL<R, true, 1, false> : &KERNEL<R, false, 1, false>;  \
+      case 10: return st_ ? &KERNEL<R, true, 2, false> : &KERNEL<R, false, 2, false>; \
+      case 11: return st_ ? &KERNEL<R, true, 4, false> : &KERNEL<R, false, 4, false>; \
+      case 12: return st_ ? &KERNEL<R, true, 8, false> : &KERNEL<R, false, 8, false>; \
+      case 13: return st_ ? &KERNEL<R, true, 16, false> : &KERNEL<R, false, 16, false>; \
+      default: return st_ ? &KERNEL<R, true, 1, true> : &KERNEL<R, false, 1, true>;   \
+    }                                                                                  \
+  }()
 
 }  // namespace
 
-size_t tile_smem_bytes(int dtype_bytes, int T, int C, int vectors) {
-  return (size_t)dtype_bytes * ((size_t)1 << T) * vectors + sizeof(uint64_t) * ((size_t)1 << (T - C)) +
-         sizeof(double) * 64;
+size_t tile_smem_bytes(int amp_bytes, int T, int C, int vectors) {
+  PassDesc pd{};
+  pd.T = T;
+  pd.C = C;
+  pd.g_begin = 0;
+  pd.g_end = G_STAGE;
+  pd.lut_count = LUT_STAGE;
+  return smem_layout(amp_bytes, pd, vectors, sizeof(double) * (NT / 32)).total;
 }
 
-size_t reverse_smem_bytes(int dtype_bytes, int T, int C) {
-  return tile_smem_bytes(dtype_bytes, T, C, 2) + sizeof(double) * RP_MAX +
-         (size_t)(dtype_bytes / 2) * (NT / 32) * M_MAX;
+size_t reverse_smem_bytes(int amp_bytes, int T, int C) {
+  PassDesc pd{};
+  pd.T = T;
+  pd.C = C;
+  pd.g_begin = 0;
+  pd.g_end = G_STAGE;
+  pd.lut_count = LUT_STAGE;
+  return smem_layout(amp_bytes, pd, 2, sizeof(double) * RP_MAX + (size_t)(amp_bytes / 2) * (NT / 32) * M_MAX)
+      .total;
 }
 
-int max_grid_blocks(int dtype_bytes, int T) {
-  // upper bound on any tile kernel's grid (for partial buffers)
-  (void)dtype_bytes;
+int max_grid_blocks(int amp_bytes, int T) {
+  (void)amp_bytes;
   (void)T;
   return sm_count() * 8;
 }
@@ -670,26 +735,16 @@ cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-static bool streaming(int n, int bytes) { return ((uint64_t)bytes << n) > (64ull << 20); }
-
 template <typename R>
-cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                         const void *lut, bool inverse, cudaStream_t st) {
+cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups, const void *lut,
+                         bool inverse, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
-  const size_t smem = tile_smem_bytes(sizeof(C2), pd.T, pd.C, 1);
-  const uint64_t ntiles = 1ull << (n - pd.T);
-  cudaError_t e;
-  if (streaming(n, sizeof(C2))) {
-    auto k = k_sweep<R, true>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    const unsigned grid = (unsigned)grid_for(ntiles, blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), inverse ? 1 : 0);
-  } else {
-    auto k = k_sweep<R, false>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    const unsigned grid = (unsigned)grid_for(ntiles, blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), inverse ? 1 : 0);
-  }
+  const size_t smem = smem_layout(sizeof(C2), pd, 1, 0).total;
+  auto k = Q2_DISPATCH(k_sweep, R, n, pd.T);
+  cudaError_t e = prepare(k, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
+  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), inverse ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -697,27 +752,20 @@ template <typename R>
 int expect_grid(int n, int T, int C) {
   using C2 = typename Vec2<R>::type;
   const size_t smem = tile_smem_bytes(sizeof(C2), T, C, 1);
-  const uint64_t ntiles = 1ull << (n - T);
-  auto k = streaming(n, sizeof(C2)) ? k_expect<R, true> : k_expect<R, false>;
-  set_smem(k, smem);
-  return (int)grid_for(ntiles, blocks_per_sm(k, smem));
+  auto k = Q2_DISPATCH(k_expect, R, n, T);
+  prepare(k, smem);
+  return (int)grid_for(1ull << (n - T), blocks_per_sm(k, smem));
 }
 
 template <typename R>
 cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
                           const void *lut, double *partial, int grid, bool first, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
-  const size_t smem = tile_smem_bytes(sizeof(C2), pd.T, pd.C, 1);
-  cudaError_t e;
-  if (streaming(n, sizeof(C2))) {
-    auto k = k_expect<R, true>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), partial, first);
-  } else {
-    auto k = k_expect<R, false>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), partial, first);
-  }
+  const size_t smem = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32)).total;
+  auto k = Q2_DISPATCH(k_expect, R, n, pd.T);
+  cudaError_t e = prepare(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), partial, first ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -730,20 +778,12 @@ template <typename R>
 cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
                           const void *lut, bool first, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
-  const size_t smem = tile_smem_bytes(sizeof(C2), pd.T, pd.C, 2);
-  const uint64_t ntiles = 1ull << (n - pd.T);
-  cudaError_t e;
-  if (streaming(n, sizeof(C2))) {
-    auto k = k_happly<R, true>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    const unsigned grid = (unsigned)grid_for(ntiles, blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), first);
-  } else {
-    auto k = k_happly<R, false>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    const unsigned grid = (unsigned)grid_for(ntiles, blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), first);
-  }
+  const size_t smem = smem_layout(sizeof(C2), pd, 2, 0).total;
+  auto k = Q2_DISPATCH(k_happly, R, n, pd.T);
+  cudaError_t e = prepare(k, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
+  k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), first ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -765,10 +805,9 @@ template <typename R>
 int reverse_grid(int n, int T, int C) {
   using C2 = typename Vec2<R>::type;
   const size_t smem = reverse_smem_bytes(sizeof(C2), T, C);
-  const uint64_t ntiles = 1ull << (n - T);
-  auto k = streaming(n, sizeof(C2)) ? k_reverse<R, true> : k_reverse<R, false>;
-  set_smem(k, smem);
-  return (int)grid_for(ntiles, blocks_per_sm(k, smem));
+  auto k = Q2_DISPATCH(k_reverse, R, n, T);
+  prepare(k, smem);
+  return (int)grid_for(1ull << (n - T), blocks_per_sm(k, smem));
 }
 
 template <typename R>
@@ -776,23 +815,13 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
                            const void *lut, const uint64_t *signmask, double *partial, double *gphi,
                            cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
-  const size_t smem = reverse_smem_bytes(sizeof(C2), pd.T, pd.C);
-  const uint64_t ntiles = 1ull << (n - pd.T);
-  cudaError_t e;
-  unsigned grid;
-  if (streaming(n, sizeof(C2))) {
-    auto k = k_reverse<R, true>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    grid = (unsigned)grid_for(ntiles, blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), signmask,
-                              partial);
-  } else {
-    auto k = k_reverse<R, false>;
-    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
-    grid = (unsigned)grid_for(ntiles, blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), signmask,
-                              partial);
-  }
+  const size_t smem =
+      smem_layout(sizeof(C2), pd, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX).total;
+  auto k = Q2_DISPATCH(k_reverse, R, n, pd.T);
+  cudaError_t e = prepare(k, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
+  k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), signmask, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nrot = pd.rot_end - pd.rot_begin;
   k_reduce_rot<<<(nrot + 127) / 128, 128, 0, st>>>(partial, (int)grid, nrot, gphi + pd.rot_begin);

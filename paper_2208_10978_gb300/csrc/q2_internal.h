@@ -40,6 +40,8 @@ constexpr int R_MAX_ROT = 6;     // max code bits of a rotation group (sign mask
 constexpr int M_MAX = 16;        // max rotations in one rotation group
 constexpr int P_MAX = 32;        // max per-thread iterations over a tile (2^T <= NT * P_MAX)
 constexpr int RP_MAX = 512;      // max rotations in one pass (reverse-sweep partials)
+constexpr int G_STAGE = 64;      // max groups per pass (staged in shared memory)
+constexpr int LUT_STAGE = 1024;  // max LUT entries per pass (staged in shared memory)
 constexpr int T_MIN = 8;
 constexpr int T_LIMIT = 13;
 
@@ -66,6 +68,7 @@ struct PassDesc {
   int C;                  // chunk = 2^C contiguous amplitudes
   int g_begin, g_end;     // groups [g_begin, g_end)
   int rot_begin, rot_end; // rotation plans: rotations covered by this pass
+  int lut_begin, lut_count;  // LUT entries of this pass's groups (contiguous)
 };
 
 // Host-side schedule of a rotation list (an ansatz or one apply call).

@@ -214,11 +214,13 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
     Gf2Basis W;
     for (int q = 0; q < C; ++q) W.add(1ull << q);
     PassRange cur{0, 0, {}};
-    int rots = 0;
+    int rots = 0, luts = 0;
     for (size_t g = 0; g < groups.size(); ++g) {
       const uint64_t xg = groups[g].x;
       const int m = (int)groups[g].members.size();
-      const bool fits = (xg == 0 || W.contains(xg) || W.rank() < T) && rots + m <= RP_MAX;
+      const int nl = 1 << groups[g].basis.rank();
+      const bool fits = (xg == 0 || W.contains(xg) || W.rank() < T) && rots + m <= RP_MAX &&
+                        (int)(g - cur.gb) < G_STAGE && luts + nl <= LUT_STAGE;
       if (!fits && g > cur.gb) {
         cur.ge = g;
         ranges.push_back(cur);
@@ -226,9 +228,11 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
         W = Gf2Basis();
         for (int q = 0; q < C; ++q) W.add(1ull << q);
         rots = 0;
+        luts = 0;
       }
       if (xg != 0 && W.add(xg)) cur.gens.push_back(xg);
       rots += m;
+      luts += nl;
     }
     if (cur.gb < groups.size()) {
       cur.ge = groups.size();
@@ -272,6 +276,8 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
       lut += ncode;
     }
     pd.g_end = (int)P.groups.size();
+    pd.lut_begin = (int)P.groups[pd.g_begin].lut;
+    pd.lut_count = (int)lut - pd.lut_begin;
     pd.rot_end = (int)(groups[pr.ge - 1].members.back() + 1);
     P.max_pass_rots = std::max(P.max_pass_rots, pd.rot_end - pd.rot_begin);
     P.passes.push_back(pd);
@@ -348,15 +354,20 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       gens.clear();
     };
     reset();
+    int luts = 0;
     for (size_t g = 0; g < groups.size(); ++g) {
       if (popc64(groups[g].x | lowmask) <= T) continue;
-      if (!W.contains(groups[g].x) && W.rank() >= T) {
+      const int nl = 1 << groups[g].basis.rank();
+      if ((!W.contains(groups[g].x) && W.rank() >= T) || (int)cur.size() >= G_STAGE ||
+          luts + nl > LUT_STAGE) {
+        luts = 0;
         pass_groups.push_back(cur);
         pass_gens.push_back(gens);
         reset();
       }
       if (W.add(groups[g].x)) gens.push_back(groups[g].x);
       cur.push_back(g);
+      luts += nl;
       done[g] = 1;
       --remaining;
     }
@@ -370,14 +381,22 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
   while (remaining > 0) {
     uint64_t L = lowmask;
     std::vector<size_t> chosen;
+    int luts = 0;
+    bool full = false;
     for (;;) {
-      for (size_t g = 0; g < groups.size(); ++g)
+      for (size_t g = 0; g < groups.size() && !full; ++g)
         if (!done[g] && (groups[g].x & ~L) == 0) {
+          const int nl = 1 << groups[g].basis.rank();
+          if ((int)chosen.size() >= G_STAGE || luts + nl > LUT_STAGE) {
+            full = true;
+            break;
+          }
           done[g] = 1;
           --remaining;
           chosen.push_back(g);
+          luts += nl;
         }
-      if (remaining == 0) break;
+      if (remaining == 0 || full) break;
       int freq[64] = {0};
       for (size_t g = 0; g < groups.size(); ++g)
         if (!done[g]) {
@@ -451,6 +470,8 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       lut += ncode;
     }
     pd.g_end = (int)H.groups.size();
+    pd.lut_begin = (int)H.groups[pd.g_begin].lut;
+    pd.lut_count = (int)lut - pd.lut_begin;
     H.passes.push_back(pd);
   }
   H.lut_entries = lut;

@@ -91,19 +91,11 @@ def _subset_groups(ham, min_terms, rng):
     return Hamiltonian(ham.n, ham.x[idx], ham.z[idx], ham.c[idx])
 
 
-def sweep32(seed=0, n=32, n_elec=16, n_rot=50_000, min_terms=30_000):
-    """32-qubit sweep workload.
-
-    Rotations: whole all-pairs excitations drawn without replacement in a
-    seeded random order, each excitation's strings emitted consecutively,
-    stopping at n_rot rotations (the last excitation may be cut short).
-    Hamiltonian: whole xmask groups of the full random-integral Hamiltonian,
-    x = 0 group first then seeded random order, until >= min_terms terms.
-    """
-    rng = np.random.default_rng([seed, 0x5EED32])
-    h, eri = random_integrals(n // 2, seed)
-    full = hamiltonian_from_integrals(h, eri)
-    ham = _subset_groups(full, min_terms, rng)
+def sweep_ansatz(n, n_elec, n_rot, seed=0):
+    """Random-order UCCSD rotation list: whole all-pairs excitations drawn
+    without replacement in a seeded order, strings emitted consecutively,
+    cut at n_rot rotations.  Returns (ansatz, theta)."""
+    rng = np.random.default_rng([seed, 0x5EED32, n])
     pool = excitations(n, n_elec, "all_pairs")
     perm = rng.permutation(len(pool))
     chosen, count = [], 0
@@ -118,7 +110,24 @@ def sweep32(seed=0, n=32, n_elec=16, n_rot=50_000, min_terms=30_000):
         keep = slice(0, n_rot)
         ans = UccsdAnsatz(n, n_elec, ans.x[keep], ans.z[keep], ans.param[keep],
                           ans.coef[keep], ans.n_params, ans.tags)
-    return Workload(f"sweep{n}", n, n_elec, h, eri, ham, ans, _theta(ans.n_params, seed))
+    return ans, _theta(ans.n_params, seed)
+
+
+def sweep32(seed=0, n=32, n_elec=16, n_rot=50_000, min_terms=30_000):
+    """32-qubit sweep workload.
+
+    Rotations: whole all-pairs excitations drawn without replacement in a
+    seeded random order, each excitation's strings emitted consecutively,
+    stopping at n_rot rotations (the last excitation may be cut short).
+    Hamiltonian: whole xmask groups of the full random-integral Hamiltonian,
+    x = 0 group first then seeded random order, until >= min_terms terms.
+    """
+    rng = np.random.default_rng([seed, 0x5EED32])
+    h, eri = random_integrals(n // 2, seed)
+    full = hamiltonian_from_integrals(h, eri)
+    ham = _subset_groups(full, min_terms, rng)
+    ans, theta = sweep_ansatz(n, n_elec, n_rot, seed)
+    return Workload(f"sweep{n}", n, n_elec, h, eri, ham, ans, theta)
 
 
 @dataclass

@@ -13,10 +13,11 @@ import ctypes
 import numpy as np
 
 PASS_DT = np.dtype([("w", "<u8", 13), ("umask", "<u8"), ("T", "<i4"), ("C", "<i4"),
-                    ("g_begin", "<i4"), ("g_end", "<i4"), ("rot_begin", "<i4"), ("rot_end", "<i4")])
+                    ("g_begin", "<i4"), ("g_end", "<i4"), ("rot_begin", "<i4"), ("rot_end", "<i4"),
+                    ("lut_begin", "<i4"), ("lut_count", "<i4")])
 GROUP_DT = np.dtype([("bp", "<u8", 8), ("xl", "<u4"), ("lut", "<u4"), ("rot0", "<u4"), ("kind", "u1"),
                      ("pivot", "u1"), ("r", "u1"), ("m", "u1"), ("jcode", "u1", 32)])
-assert PASS_DT.itemsize == 136 and GROUP_DT.itemsize == 112
+assert PASS_DT.itemsize == 144 and GROUP_DT.itemsize == 112
 
 DIAG, REAL, XROT, PAIR = 0, 1, 2, 3
 
