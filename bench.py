@@ -354,9 +354,10 @@ def plan_bytes(lib, w, dtype):
     from tests import plan_emulator as emu
     amp = 8 if dtype == "complex64" else 16
     T, C = (12, 4) if dtype == "complex64" else (11, 3)
-    hp, hg, hl = emu.ham_plan(lib, w.n, w.ham.x, w.ham.z, w.ham.c, T, C)
-    rp, rg, rl, sm = emu.rot_plan(lib, w.n, w.ansatz.x, w.ansatz.z, w.angles(), T, C)
-    return int(112 * (len(hg) + len(rg)) + amp * (len(hl) + len(rl)) + 8 * len(sm))
+    hp, hg, hb, hl = emu.ham_plan(lib, w.n, w.ham.x, w.ham.z, w.ham.c, T, C)
+    rp, rg, rb, rl, sm = emu.rot_plan(lib, w.n, w.ansatz.x, w.ansatz.z, w.angles(), T, C)
+    return int(emu.GROUP_DT.itemsize * (len(hg) + len(rg)) + emu.BLOCK_DT.itemsize * (len(hb) + len(rb))
+               + amp * (len(hl) + len(rl)) + 8 * len(sm))
 
 
 if __name__ == "__main__":

@@ -7,17 +7,23 @@
  * The paper has no counterpart: they describe this library's tiling of the
  * state vector, not the method.
  *
- * Layouts (little endian, packed as below):
- *   q2_pass   (144 bytes): uint64 w[13] local basis; uint64 umask; int32 T, C,
- *             g_begin, g_end, rot_begin, rot_end, lut_begin, lut_count.
- *   q2_group  (112 bytes): uint64 bp[8] code basis in packed-index space;
- *             uint32 xl, lut, rot0; uint8 kind, pivot, r, m; uint8 jcode[32].
- * counts[0..2] = number of passes, groups, LUT entries.  Output arrays may be
- * NULL (sizes only); otherwise they must hold counts[] entries.  lut2 holds
- * two doubles per entry: (cos, sin) of the combined angle for rotation plans,
- * (R, Q) combined coefficients for Hamiltonian plans.  signmask (rotation
- * plans, n_rot entries): bit c set iff rotation k enters its group's angle
- * with a minus sign at code c.
+ * Layouts (little endian, packed as below; see the library's q2_internal.h):
+ *   q2_pass  (152 bytes): uint64 w[13] local basis; uint64 umask; int32 T, C,
+ *            g_begin, g_end, rot_begin, rot_end, lut_begin, lut_count,
+ *            b_begin, b_end.
+ *   q2_group (272 bytes): uint64 bp[8] code basis in packed-index space;
+ *            uint32 xl, lut, rot0; uint8 kind, r, m, a; uint8 bjcode[16],
+ *            bccode[16], blane[32], bwarp[8] (register-block enumeration);
+ *            uint8 pivot, pad[7], pjcode[32], plane[32], pwarp[8]; uint16 pu[16]
+ *            (pair enumeration); uint8 pad[8].
+ *   q2_block (80 bytes): uint16 comb[16], uj[16]; uint8 d, piv[4], pad[3];
+ *            uint16 g_begin, g_end; uint8 pad[4].
+ * counts[0..3] = number of passes, groups, LUT entries, register blocks.
+ * Output arrays may be NULL (sizes only); otherwise they must hold counts[]
+ * entries.  lut2 holds two doubles per entry: (cos, sin) of the combined
+ * angle for rotation plans, (R, Q) combined coefficients for Hamiltonian
+ * plans.  signmask (rotation plans, n_rot entries): bit c set iff rotation k
+ * enters its group's angle with a minus sign at code c.
  * Errors: Q2_ERR_INVALID for bad sizes or masks (see q2.h).
  */
 #ifndef Q2_DEBUG_H
@@ -31,12 +37,13 @@ extern "C" {
 
 q2_status q2_debug_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z,
                             const double *angles, int tile_qubits, int chunk_qubits,
-                            int64_t *counts, void *passes, void *groups, double *lut2,
-                            uint64_t *signmask);
+                            int64_t *counts, void *passes, void *groups, void *blocks,
+                            double *lut2, uint64_t *signmask);
 
 q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z,
                             const double *coef, int tile_qubits, int chunk_qubits,
-                            int64_t *counts, void *passes, void *groups, double *lut2);
+                            int64_t *counts, void *passes, void *groups, void *blocks,
+                            double *lut2);
 
 /* Threads per CTA of the tile kernels (the per-thread offsets of q2_group.jcode use it). */
 int q2_debug_threads_per_cta(void);

@@ -110,13 +110,16 @@ struct DevTables {
   int device = -1;
   int T = 0;
   GroupDesc *groups = nullptr;
+  BlockDesc *blocks = nullptr;
   void *lut = nullptr;          // Hamiltonian LUT in the dtype's precision
   uint64_t *signmask = nullptr; // rotation sign masks
   void release() {
     if (groups) cudaFree(groups);
+    if (blocks) cudaFree(blocks);
     if (lut) cudaFree(lut);
     if (signmask) cudaFree(signmask);
     groups = nullptr;
+    blocks = nullptr;
     lut = nullptr;
     signmask = nullptr;
     ready = false;
@@ -182,14 +185,19 @@ q2_status ham_tables(const q2_ham *hc, q2_dtype d, const HamPlan **plan, const D
     const HamPlan &p = h->plan[d];
     const size_t gb = sizeof(GroupDesc) * std::max<size_t>(1, p.groups.size());
     std::vector<unsigned char> lb = lut_bytes(p.lut2, d);
+    const size_t bb = sizeof(BlockDesc) * std::max<size_t>(1, p.blocks.size());
     Q2_CUDA(cudaMalloc(&t.groups, gb), "cudaMalloc(groups)");
-    if (cudaMalloc(&t.lut, std::max<size_t>(16, lb.size())) != cudaSuccess) {
+    if (cudaMalloc(&t.lut, std::max<size_t>(16, lb.size())) != cudaSuccess ||
+        cudaMalloc(&t.blocks, bb) != cudaSuccess) {
       t.release();
-      return fail(Q2_ERR_OOM, "cudaMalloc(Hamiltonian LUT)");
+      return fail(Q2_ERR_OOM, "cudaMalloc(Hamiltonian tables)");
     }
     if (!p.groups.empty())
       Q2_CUDA(cudaMemcpy(t.groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size(),
                          cudaMemcpyHostToDevice), "upload groups");
+    if (!p.blocks.empty())
+      Q2_CUDA(cudaMemcpy(t.blocks, p.blocks.data(), sizeof(BlockDesc) * p.blocks.size(),
+                         cudaMemcpyHostToDevice), "upload blocks");
     if (!lb.empty()) Q2_CUDA(cudaMemcpy(t.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice), "upload LUT");
     t.device = device;
     t.T = p.T;
@@ -224,14 +232,18 @@ q2_status ansatz_tables(const q2_ansatz *ac, q2_dtype d, const RotPlan **plan, c
     const RotPlan &p = a->plan[d];
     const size_t gb = sizeof(GroupDesc) * std::max<size_t>(1, p.groups.size());
     const size_t sb = sizeof(uint64_t) * std::max<size_t>(1, p.signmask.size());
+    const size_t bb = sizeof(BlockDesc) * std::max<size_t>(1, p.blocks.size());
     Q2_CUDA(cudaMalloc(&t.groups, gb), "cudaMalloc(groups)");
-    if (cudaMalloc(&t.signmask, sb) != cudaSuccess) {
+    if (cudaMalloc(&t.signmask, sb) != cudaSuccess || cudaMalloc(&t.blocks, bb) != cudaSuccess) {
       t.release();
-      return fail(Q2_ERR_OOM, "cudaMalloc(sign masks)");
+      return fail(Q2_ERR_OOM, "cudaMalloc(rotation tables)");
     }
     if (!p.groups.empty())
       Q2_CUDA(cudaMemcpy(t.groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size(),
                          cudaMemcpyHostToDevice), "upload groups");
+    if (!p.blocks.empty())
+      Q2_CUDA(cudaMemcpy(t.blocks, p.blocks.data(), sizeof(BlockDesc) * p.blocks.size(),
+                         cudaMemcpyHostToDevice), "upload blocks");
     if (!p.signmask.empty())
       Q2_CUDA(cudaMemcpy(t.signmask, p.signmask.data(), sizeof(uint64_t) * p.signmask.size(),
                          cudaMemcpyHostToDevice), "upload sign masks");
@@ -245,10 +257,10 @@ q2_status ansatz_tables(const q2_ansatz *ac, q2_dtype d, const RotPlan **plan, c
 }
 
 template <typename R>
-cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups, const void *dlut,
-                      bool inverse, cudaStream_t st) {
+cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups, const BlockDesc *dblocks,
+                      const void *dlut, cudaStream_t st) {
   for (const PassDesc &pd : p.passes) {
-    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dlut, inverse, st);
+    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dblocks, dlut, false, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -258,7 +270,7 @@ template <typename R>
 cudaError_t run_expect(const R *psi, int n, const HamPlan &h, const DevTables &t, double *partial,
                        int grid, double *out2, cudaStream_t st) {
   for (size_t i = 0; i < h.passes.size(); ++i) {
-    cudaError_t e = launch_expect<R>(psi, n, h.passes[i], t.groups, t.lut, partial, grid, i == 0, st);
+    cudaError_t e = launch_expect<R>(psi, n, h.passes[i], t.groups, t.blocks, t.lut, partial, grid, i == 0, st);
     if (e != cudaSuccess) return e;
   }
   return launch_reduce_pairs(partial, grid, out2, st);
@@ -336,7 +348,7 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
   if (timing) Q2_CUDA(g_timing.ensure(), "timing events");
   Q2_CUDA(launch_init_hf<R>(psi, n, a->n_elec, st), "init_hf");
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[0], st), "event");
-  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, base + L.lut, false, st), "sweep");
+  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, rt->blocks, base + L.lut, st), "sweep");
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[1], st), "event");
   double host_out[2] = {0, 0};
   g_timing.counts[0] = (double)rp->passes.size();
@@ -434,15 +446,19 @@ q2_status q2_apply_pauli_rotations(void *psi_dev, int n, q2_dtype dtype, const u
   std::vector<unsigned char> lb = lut_bytes(lut2, dtype);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t gb = align_up(sizeof(GroupDesc) * p.groups.size(), 256);
+  const size_t bb = align_up(sizeof(BlockDesc) * p.blocks.size(), 256);
   unsigned char *tmp = nullptr;
-  Q2_CUDA(cudaMallocAsync((void **)&tmp, gb + lb.size(), st), "cudaMallocAsync(schedule)");
+  Q2_CUDA(cudaMallocAsync((void **)&tmp, gb + bb + lb.size(), st), "cudaMallocAsync(schedule)");
   cudaError_t e = cudaMemcpyAsync(tmp, p.groups.data(), sizeof(GroupDesc) * p.groups.size(),
                                   cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + gb, lb.data(), lb.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tmp + gb, p.blocks.data(), sizeof(BlockDesc) * p.blocks.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + gb + bb, lb.data(), lb.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     const GroupDesc *dg = reinterpret_cast<const GroupDesc *>(tmp);
-    e = dtype == Q2_C64 ? run_sweep<float>(static_cast<float *>(psi_dev), n, p, dg, tmp + gb, false, st)
-                        : run_sweep<double>(static_cast<double *>(psi_dev), n, p, dg, tmp + gb, false, st);
+    const BlockDesc *db = reinterpret_cast<const BlockDesc *>(tmp + gb);
+    e = dtype == Q2_C64 ? run_sweep<float>(static_cast<float *>(psi_dev), n, p, dg, db, tmp + gb + bb, st)
+                        : run_sweep<double>(static_cast<double *>(psi_dev), n, p, dg, db, tmp + gb + bb, st);
   }
   cudaFreeAsync(tmp, st);
   if (e != cudaSuccess) return cuda_fail(e, "apply_pauli_rotations");
@@ -636,13 +652,13 @@ q2_status q2_batch_energy_grad(int n_requests, const q2_ansatz *const *ansatz, c
 
 #include "../../include/q2_debug.h"
 
-static_assert(sizeof(PassDesc) == 144, "q2_pass layout");
+static_assert(sizeof(PassDesc) == 152, "q2_pass layout");
 
 extern "C" {
 
 q2_status q2_debug_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, const double *angles,
                             int tile_qubits, int chunk_qubits, int64_t *counts, void *passes, void *groups,
-                            double *lut2, uint64_t *signmask) {
+                            void *blocks, double *lut2, uint64_t *signmask) {
   if (n < 1 || n > 34 || !counts) return fail(Q2_ERR_INVALID, "bad arguments");
   if (tile_qubits < 1 || tile_qubits > T_LIMIT || chunk_qubits < 1) return fail(Q2_ERR_INVALID, "bad tile shape");
   q2_status s = check_masks(n, n_rot, x, z, "rotations");
@@ -656,8 +672,10 @@ q2_status q2_debug_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint6
   counts[0] = (int64_t)p.passes.size();
   counts[1] = (int64_t)p.groups.size();
   counts[2] = p.lut_entries;
+  counts[3] = (int64_t)p.blocks.size();
   if (passes) std::memcpy(passes, p.passes.data(), sizeof(PassDesc) * p.passes.size());
   if (groups) std::memcpy(groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size());
+  if (blocks) std::memcpy(blocks, p.blocks.data(), sizeof(BlockDesc) * p.blocks.size());
   if (lut2) {
     if ((s = check_finite(n_rot, angles, "angles")) != Q2_OK) return s;
     p.build_lut(angles, lut2);
@@ -668,7 +686,7 @@ q2_status q2_debug_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint6
 
 q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z, const double *coef,
                             int tile_qubits, int chunk_qubits, int64_t *counts, void *passes, void *groups,
-                            double *lut2) {
+                            void *blocks, double *lut2) {
   if (n < 1 || n > 34 || !counts) return fail(Q2_ERR_INVALID, "bad arguments");
   if (tile_qubits < 1 || tile_qubits > T_LIMIT || chunk_qubits < 1) return fail(Q2_ERR_INVALID, "bad tile shape");
   q2_status s = check_masks(n, n_terms, x, z, "Hamiltonian");
@@ -683,8 +701,10 @@ q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uin
   counts[0] = (int64_t)p.passes.size();
   counts[1] = (int64_t)p.groups.size();
   counts[2] = p.lut_entries;
+  counts[3] = (int64_t)p.blocks.size();
   if (passes) std::memcpy(passes, p.passes.data(), sizeof(PassDesc) * p.passes.size());
   if (groups) std::memcpy(groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size());
+  if (blocks) std::memcpy(blocks, p.blocks.data(), sizeof(BlockDesc) * p.blocks.size());
   if (lut2) std::memcpy(lut2, p.lut2.data(), sizeof(double) * p.lut2.size());
   return Q2_OK;
 }

@@ -6,12 +6,15 @@
 // groups of the pass there, and writes the tile back (or only reduces it).
 // Tiles are cosets of the pass's local subspace W (see q2_internal.h), so a
 // pass touches every amplitude exactly once and tiles never overlap.  The
-// pass's group descriptors and LUT are staged in shared memory once per CTA.
+// pass's offsets, group and block descriptors and LUT are staged in shared
+// memory once per CTA.
 //
-// Work split inside a tile: pair q = tid + NT*j (j < P) of a group with pivot
-// p is local index insert_zero(q, p) and its partner ^ xl; P = 2^(T-1)/NT is
-// a compile-time constant, so the j loop unrolls and its LUT reads are
-// independent.  Tiles smaller than 2 * NT amplitudes take a guarded P = 1.
+// Sweep and expectation work on register blocks: for each block of groups
+// whose xmasks span d local dimensions, a thread loads a 2^d-amplitude coset
+// into registers, applies (or evaluates) every group of the block there with
+// compile-time pair indices, and writes it back once.  H apply and the
+// reverse sweep walk one group at a time (pair q = tid + NT*j).  Codes come
+// from host tables plus one per-tile code per group.
 //
 //   k_init_hf     HF determinant (Eq. jw-wfn-map)
 //   k_sweep       rotation groups, forward or inverse (product formula after Eq. ucc)
@@ -54,9 +57,9 @@ __device__ __forceinline__ void st16(V *p, V v) {
 
 // ------------------------------------------------------------------ shared-memory layout
 
-// [tiles: vectors * 2^T amplitudes][off: 2^(T-C) u64][groups][lut][extra]
+// [tiles: vectors * 2^T amplitudes][off: 2^(T-C) u64][groups][blocks][lut][tcode][extra]
 struct SmemLayout {
-  size_t tiles, off, groups, lut, extra, total;
+  size_t tiles, off, groups, blocks, lut, tcode, extra, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -71,30 +74,45 @@ __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc 
   o = align16(o + sizeof(uint64_t) * ((size_t)1 << (pd.T - pd.C)));
   L.groups = o;
   o = align16(o + sizeof(GroupDesc) * (size_t)(pd.g_end - pd.g_begin));
+  L.blocks = o;
+  o = align16(o + sizeof(BlockDesc) * (size_t)(pd.b_end - pd.b_begin));
   L.lut = o;
   o = align16(o + (size_t)amp_bytes * (size_t)pd.lut_count);
+  L.tcode = o;
+  o = align16(o + sizeof(uint32_t) * (size_t)(pd.g_end - pd.g_begin));
   L.extra = o;
   o = align16(o + extra_bytes);
   L.total = o;
   return L;
 }
 
-template <typename R> struct Tile {
+template <typename R> struct Stage {
   using C2 = typename Vec2<R>::type;
   int T, C;
   uint32_t amps;
   uint64_t *off;
   const GroupDesc *gs;   // staged groups of the pass (index g - g_begin)
-  const C2 *lut;         // staged LUT (index lut - lut_begin)
+  const BlockDesc *bs;   // staged blocks of the pass (index b - b_begin)
+  const C2 *lut;         // staged LUT, indexed by the global LUT offset
+  uint32_t *tcode;       // per-tile code of each group
 };
 
-// Stage offsets, group descriptors and LUT of a pass; caller syncs.
+template <typename T>
+__device__ __forceinline__ void copy16(void *dst, const T *src, int count) {
+  uint4 *d = reinterpret_cast<uint4 *>(dst);
+  const uint4 *s = reinterpret_cast<const uint4 *>(src);
+  const int n16 = count * (int)(sizeof(T) / 16);
+  for (int i = threadIdx.x; i < n16; i += NT) d[i] = __ldg(s + i);
+}
+
+// Stage offsets, descriptors and LUT of a pass; caller syncs.
 template <typename R>
-__device__ __forceinline__ Tile<R> stage_pass(unsigned char *smem, const PassDesc &pd,
-                                              const SmemLayout &L, const GroupDesc *groups,
-                                              const typename Vec2<R>::type *lut) {
+__device__ __forceinline__ Stage<R> stage_pass(unsigned char *smem, const PassDesc &pd,
+                                               const SmemLayout &L, const GroupDesc *groups,
+                                               const BlockDesc *blocks,
+                                               const typename Vec2<R>::type *lut) {
   using C2 = typename Vec2<R>::type;
-  Tile<R> t;
+  Stage<R> t;
   t.T = pd.T;
   t.C = pd.C;
   t.amps = 1u << pd.T;
@@ -106,32 +124,49 @@ __device__ __forceinline__ Tile<R> stage_pass(unsigned char *smem, const PassDes
       if ((h >> b) & 1) o ^= pd.w[pd.C + b];
     t.off[h] = o;
   }
-  const int ng = pd.g_end - pd.g_begin;
-  uint4 *gd = reinterpret_cast<uint4 *>(smem + L.groups);
-  const uint4 *gsrc = reinterpret_cast<const uint4 *>(groups + pd.g_begin);
-  for (int i = threadIdx.x; i < ng * (int)(sizeof(GroupDesc) / 16); i += NT) gd[i] = __ldg(gsrc + i);
+  copy16(smem + L.groups, groups + pd.g_begin, pd.g_end - pd.g_begin);
+  if (blocks) copy16(smem + L.blocks, blocks + pd.b_begin, pd.b_end - pd.b_begin);
   C2 *ld = reinterpret_cast<C2 *>(smem + L.lut);
   for (int i = threadIdx.x; i < pd.lut_count; i += NT) ld[i] = __ldg(lut + pd.lut_begin + i);
   t.gs = reinterpret_cast<const GroupDesc *>(smem + L.groups);
+  t.bs = reinterpret_cast<const BlockDesc *>(smem + L.blocks);
   t.lut = ld - pd.lut_begin;
+  t.tcode = reinterpret_cast<uint32_t *>(smem + L.tcode);
   return t;
+}
+
+// Tile part of every group's code for tile t (threads g < ng); caller syncs.
+template <typename R>
+__device__ __forceinline__ void tile_codes(const Stage<R> &s, int ng, uint64_t t) {
+  const int g = threadIdx.x;
+  if (g < ng) {
+    const GroupDesc &d = s.gs[g];
+    const uint64_t packed = t << s.T;
+    uint32_t c = 0;
+    for (int k = 0; k < d.r; ++k) c |= (uint32_t)par64(packed & d.bp[k]) << k;
+    s.tcode[g] = c;
+  }
 }
 
 __device__ __forceinline__ uint64_t tile_base(uint64_t t, uint64_t umask) { return deposit_bits(t, umask); }
 
-// Gather one tile of `src` into shared memory.
+// Gather one tile of `src` into shared memory (LOAD_BATCH 16-byte loads in flight per thread).
+#ifndef Q2_LOAD_BATCH
+#define Q2_LOAD_BATCH 4
+#endif
+constexpr int LOAD_BATCH = Q2_LOAD_BATCH;
 template <typename R, bool STREAM>
-__device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Tile<R> &tc,
+__device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Stage<R> &tc,
                                           typename Vec16<R>::type *dst) {
   using V = typename Vec16<R>::type;
   constexpr int A = Vec16<R>::amps;
   const uint32_t nv = tc.amps / A;
   const uint32_t cm = (1u << tc.C) - 1u;
   const V *g = reinterpret_cast<const V *>(src);
-  for (uint32_t v0 = 0; v0 < nv; v0 += 8 * NT) {
-    V buf[8];
+  for (uint32_t v0 = 0; v0 < nv; v0 += LOAD_BATCH * NT) {
+    V buf[LOAD_BATCH];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < LOAD_BATCH; ++k) {
       const uint32_t v = v0 + k * NT + threadIdx.x;
       if (v < nv) {
         const uint32_t l = v * A;
@@ -140,7 +175,7 @@ __device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Til
       }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < LOAD_BATCH; ++k) {
       const uint32_t v = v0 + k * NT + threadIdx.x;
       if (v < nv) dst[v] = buf[k];
     }
@@ -148,7 +183,7 @@ __device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Til
 }
 
 template <typename R, bool STREAM>
-__device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Tile<R> &tc,
+__device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Stage<R> &tc,
                                            const typename Vec16<R>::type *src) {
   using V = typename Vec16<R>::type;
   constexpr int A = Vec16<R>::amps;
@@ -163,23 +198,25 @@ __device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Tile<R>
   }
 }
 
-// Code of the thread's first element of a group in the current tile.
-__device__ __forceinline__ uint32_t thread_code(const GroupDesc &d, int r, uint64_t packed) {
-  uint32_t code = 0;
-  for (int l = 0; l < r; ++l) code |= (uint32_t)par64(packed & d.bp[l]) << l;
-  return code;
-}
+// ------------------------------------------------------------------ complex helpers
 
-// Work assignment of one group for a thread: local indices of its P pairs
-// (or 2P diagonal amplitudes) and their codes.
-template <int P, bool GUARD>
-struct PairIter {
-  uint32_t li0, code0;
-  int pivot;
-  __device__ __forceinline__ uint32_t li(int j) const {
-    return li0 | insert_zero((uint32_t)(NT * j), pivot);
-  }
-};
+template <typename C2, typename R>
+__device__ __forceinline__ void rot_real(C2 &a, C2 &b, R c, R s) {   // [[c,-s],[s,c]]
+  const C2 x = a, y = b;
+  a = C2{c * x.x - s * y.x, c * x.y - s * y.y};
+  b = C2{s * x.x + c * y.x, s * x.y + c * y.y};
+}
+template <typename C2, typename R>
+__device__ __forceinline__ void rot_xrot(C2 &a, C2 &b, R c, R s) {   // c - i s X
+  const C2 x = a, y = b;
+  a = C2{c * x.x + s * y.y, c * x.y - s * y.x};
+  b = C2{c * y.x + s * x.y, c * y.y - s * x.x};
+}
+template <typename C2, typename R>
+__device__ __forceinline__ void phase(C2 &a, R c, R s) {               // (c - i s) a
+  const C2 x = a;
+  a = C2{c * x.x + s * x.y, c * x.y - s * x.x};
+}
 
 // ------------------------------------------------------------------ init
 
@@ -199,82 +236,128 @@ __global__ void k_init_hf(R *psi, uint64_t n_amps, uint64_t hf) {
   }
 }
 
-// ------------------------------------------------------------------ rotation sweep
+// ------------------------------------------------------------------ register blocks
 
-// Apply one rotation group (sign +1 forward, -1 inverse) to a shared-memory tile.
-template <typename R, int P, bool GUARD>
-__device__ __forceinline__ void rot_group(typename Vec2<R>::type *tile, const GroupDesc &d,
-                                          const Tile<R> &tc, uint64_t tpacked, R sgn) {
-  using C2 = typename Vec2<R>::type;
-  const int kind = d.kind;
-  const int r = d.r;
-  const C2 *lut = tc.lut + d.lut;
-  const uint32_t tid = threadIdx.x;
-  if (kind == KIND_DIAG) {
-    const uint32_t code0 = thread_code(d, r, tpacked | tid);
+// Cosets per thread of a D-dimensional block in a 2^TT tile (TT >= D + 8).
+template <int TT, int D> struct BlockShape {
+  static constexpr int J = (1 << (TT - D)) / NT;
+  static constexpr int N = 1 << D;
+};
+
+// Rotate the pairs (c, c ^ A) of a coset held in registers.
+template <typename R, int D, int A>
+__device__ __forceinline__ void coset_pairs(typename Vec2<R>::type (&v)[1 << D], const GroupDesc &g,
+                                            const typename Vec2<R>::type *L, uint32_t cb, R sgn,
+                                            bool real) {
+  constexpr int HB = 31 - __builtin_clz(A);
 #pragma unroll
-    for (int j = 0; j < 2 * P; ++j) {
-      const uint32_t l = tid + NT * j;
-      if (GUARD && l >= tc.amps) break;
-      const C2 cs = lut[code0 ^ d.jcode[j]];
-      const R c = cs.x, s = sgn * cs.y;
-      const C2 a = tile[l];
-      tile[l] = C2{c * a.x + s * a.y, c * a.y - s * a.x};
-    }
-    return;
+  for (int c = 0; c < (1 << D); ++c) {
+    if ((c >> HB) & 1) continue;
+    const auto cs = L[cb ^ g.bccode[c]];
+    if (real) rot_real(v[c], v[c ^ A], cs.x, sgn * cs.y);
+    else rot_xrot(v[c], v[c ^ A], cs.x, sgn * cs.y);
   }
-  const int pivot = d.pivot;
-  const uint32_t xl = d.xl;
-  if (GUARD && tid >= (tc.amps >> 1)) return;
-  const uint32_t li0 = insert_zero(tid, pivot);
-  const uint32_t code0 = thread_code(d, r, tpacked | li0);
-  if (kind == KIND_REAL) {
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
-      const C2 cs = lut[code0 ^ d.jcode[j]];
-      const R c = cs.x, s = sgn * cs.y;
-      const C2 a = tile[li], b = tile[lj];
-      tile[li] = C2{c * a.x - s * b.x, c * a.y - s * b.y};
-      tile[lj] = C2{s * a.x + c * b.x, s * a.y + c * b.y};
+}
+
+template <typename R, int D, int A>
+__device__ __forceinline__ void coset_pairs_any(int a, typename Vec2<R>::type (&v)[1 << D],
+                                                const GroupDesc &g, const typename Vec2<R>::type *L,
+                                                uint32_t cb, R sgn, bool real) {
+  if constexpr (A < (1 << D)) {
+    if (a == A) {
+      coset_pairs<R, D, A>(v, g, L, cb, sgn, real);
+      return;
     }
-  } else {
+    coset_pairs_any<R, D, A + 1>(a, v, g, L, cb, sgn, real);
+  }
+}
+
+// One register block of the sweep.  J cosets per thread (GUARD: at most one).
+template <typename R, int D, int J, bool GUARD>
+__device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const BlockDesc &B,
+                                            const Stage<R> &s, R sgn, bool inverse) {
+  using C2 = typename Vec2<R>::type;
+  constexpr int N = 1 << D;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (GUARD && tid >= (s.amps >> D)) return;
+  uint32_t bt = tid;
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
-      const C2 cs = lut[code0 ^ d.jcode[j]];
-      const R c = cs.x, s = sgn * cs.y;
-      const C2 a = tile[li], b = tile[lj];
-      tile[li] = C2{c * a.x + s * b.y, c * a.y - s * b.x};
-      tile[lj] = C2{c * b.x + s * a.y, c * b.y - s * a.x};
+  for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
+  const int gb = B.g_begin, ge = B.g_end;
+#pragma unroll 1
+  for (int j = 0; j < J; ++j) {
+    const uint32_t bj = bt ^ B.uj[j];
+    C2 v[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
+    for (int k = 0; k < ge - gb; ++k) {
+      const int gi = inverse ? ge - 1 - k : gb + k;
+      const GroupDesc &g = s.gs[gi];
+      const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
+      const C2 *L = s.lut + g.lut;
+      if (g.kind == KIND_DIAG) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const C2 cs = L[cb ^ g.bccode[c]];
+          phase(v[c], cs.x, sgn * cs.y);
+        }
+      } else {
+        coset_pairs_any<R, D, 1>(g.a, v, g, L, cb, sgn, g.kind == KIND_REAL);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < N; ++c) tile[bj ^ B.comb[c]] = v[c];
+  }
+}
+
+template <typename R, int TT, bool GUARD>
+__device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, const BlockDesc &B,
+                                                const Stage<R> &s, R sgn, bool inverse) {
+  if constexpr (GUARD) {
+    sweep_block<R, 1, 1, true>(tile, B, s, sgn, inverse);
+  } else {
+    switch (B.d) {
+      case 1: sweep_block<R, 1, BlockShape<TT, 1>::J, false>(tile, B, s, sgn, inverse); break;
+      case 2:
+        if constexpr (TT >= 10) sweep_block<R, 2, BlockShape<TT, 2>::J, false>(tile, B, s, sgn, inverse);
+        break;
+      case 3:
+        if constexpr (TT >= 11) sweep_block<R, 3, BlockShape<TT, 3>::J, false>(tile, B, s, sgn, inverse);
+        break;
+      case 4:
+        if constexpr (TT >= 12) sweep_block<R, 4, BlockShape<TT, 4>::J, false>(tile, B, s, sgn, inverse);
+        break;
     }
   }
 }
 
-template <typename R, bool STREAM, int P, bool GUARD>
-__global__ void __launch_bounds__(NT, 4) k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups,
+// ------------------------------------------------------------------ rotation sweep
+
+template <typename R, bool STREAM, int TT, bool GUARD>
+__global__ void __launch_bounds__(NT, 3) k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups,
+                                                 const BlockDesc *blocks,
                                                  const typename Vec2<R>::type *lut, int inverse) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(sizeof(C2), pd, 1, 0);
-  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+  const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
   C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   const R sgn = inverse ? (R)-1 : (R)1;
-  const int ng = pd.g_end - pd.g_begin;
+  const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
-    load_tile<R, STREAM>(psi, base, tc, reinterpret_cast<V *>(tile));
+    load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tile));
+    tile_codes(st, ng, t);
     __syncthreads();
-    const uint64_t tpacked = t << pd.T;
-    for (int k = 0; k < ng; ++k) {
-      const int g = inverse ? ng - 1 - k : k;
-      rot_group<R, P, GUARD>(tile, tc.gs[g], tc, tpacked, sgn);
+    for (int k = 0; k < nb; ++k) {
+      const int b = inverse ? nb - 1 - k : k;
+      sweep_block_any<R, TT, GUARD>(tile, st.bs[b], st, sgn, inverse != 0);
       __syncthreads();
     }
-    store_tile<R, STREAM>(psi, base, tc, reinterpret_cast<const V *>(tile));
+    store_tile<R, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
     __syncthreads();
   }
 }
@@ -308,73 +391,116 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 
 // ------------------------------------------------------------------ expectation
 
-template <typename R, bool STREAM, int P, bool GUARD>
-__global__ void __launch_bounds__(NT, 4) k_expect(const R *psi, int n, PassDesc pd,
-                                                  const GroupDesc *groups,
+template <typename R, int D, int A>
+__device__ __forceinline__ R coset_expect(const typename Vec2<R>::type (&v)[1 << D], const GroupDesc &g,
+                                          const typename Vec2<R>::type *L, uint32_t cb) {
+  constexpr int HB = 31 - __builtin_clz(A);
+  R s = 0;
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    if ((c >> HB) & 1) continue;
+    const auto rq = L[cb ^ g.bccode[c]];
+    const auto a = v[c], b = v[c ^ A];
+    // w = conj(a) b ; contribution 2 (R Re w + Q Im w), factor 2 applied by the caller
+    s += rq.x * (a.x * b.x + a.y * b.y) + rq.y * (a.x * b.y - a.y * b.x);
+  }
+  return s;
+}
+
+template <typename R, int D, int A>
+__device__ __forceinline__ R coset_expect_any(int a, const typename Vec2<R>::type (&v)[1 << D],
+                                              const GroupDesc &g, const typename Vec2<R>::type *L,
+                                              uint32_t cb) {
+  if constexpr (A < (1 << D)) {
+    if (a == A) return coset_expect<R, D, A>(v, g, L, cb);
+    return coset_expect_any<R, D, A + 1>(a, v, g, L, cb);
+  } else {
+    return (R)0;
+  }
+}
+
+template <typename R, int D, int J, bool GUARD>
+__device__ __forceinline__ void expect_block(const typename Vec2<R>::type *tile, const BlockDesc &B,
+                                             const Stage<R> &s, Kahan<R> &acc) {
+  using C2 = typename Vec2<R>::type;
+  constexpr int N = 1 << D;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (GUARD && tid >= (s.amps >> D)) return;
+  uint32_t bt = tid;
+#pragma unroll
+  for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
+  const int gb = B.g_begin, ge = B.g_end;
+#pragma unroll 1
+  for (int j = 0; j < J; ++j) {
+    const uint32_t bj = bt ^ B.uj[j];
+    C2 v[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
+    for (int gi = gb; gi < ge; ++gi) {
+      const GroupDesc &g = s.gs[gi];
+      const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
+      const C2 *L = s.lut + g.lut;
+      R e = 0;
+      if (g.kind == KIND_DIAG) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) e += L[cb ^ g.bccode[c]].x * (v[c].x * v[c].x + v[c].y * v[c].y);
+      } else {
+        e = 2 * coset_expect_any<R, D, 1>(g.a, v, g, L, cb);
+      }
+      acc.add(e);
+    }
+  }
+}
+
+template <typename R, int TT, bool GUARD>
+__device__ __forceinline__ void expect_block_any(const typename Vec2<R>::type *tile, const BlockDesc &B,
+                                                 const Stage<R> &s, Kahan<R> &acc) {
+  if constexpr (GUARD) {
+    expect_block<R, 1, 1, true>(tile, B, s, acc);
+  } else {
+    switch (B.d) {
+      case 1: expect_block<R, 1, BlockShape<TT, 1>::J, false>(tile, B, s, acc); break;
+      case 2:
+        if constexpr (TT >= 10) expect_block<R, 2, BlockShape<TT, 2>::J, false>(tile, B, s, acc);
+        break;
+      case 3:
+        if constexpr (TT >= 11) expect_block<R, 3, BlockShape<TT, 3>::J, false>(tile, B, s, acc);
+        break;
+
+    }
+  }
+}
+
+template <typename R, bool STREAM, int TT, bool GUARD>
+__global__ void __launch_bounds__(NT, 2) k_expect(const R *psi, int n, PassDesc pd,
+                                                  const GroupDesc *groups, const BlockDesc *blocks,
                                                   const typename Vec2<R>::type *lut, double *partial,
                                                   int first_pass) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32));
-  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+  const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
   C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   double *red = reinterpret_cast<double *>(smem + L.extra);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
-  const int ng = pd.g_end - pd.g_begin;
-  const uint32_t tid = threadIdx.x;
+  const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   Kahan<R> acc_e, acc_n;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
-    load_tile<R, STREAM>(psi, base, tc, reinterpret_cast<V *>(tile));
+    load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tile));
+    tile_codes(st, ng, t);
     __syncthreads();
-    const uint64_t tpacked = t << pd.T;
     if (first_pass) {
       R s = 0;
-#pragma unroll
-      for (int j = 0; j < 2 * P; ++j) {
-        const uint32_t l = tid + NT * j;
-        if (GUARD && l >= tc.amps) break;
+      for (uint32_t l = threadIdx.x; l < st.amps; l += NT) {
         const C2 a = tile[l];
         s += a.x * a.x + a.y * a.y;
       }
       acc_n.add(s);
     }
-    for (int k = 0; k < ng; ++k) {
-      const GroupDesc &d = tc.gs[k];
-      const C2 *lt = tc.lut + d.lut;
-      const int r = d.r;
-      R s = 0;
-      if (d.kind == KIND_DIAG) {
-        const uint32_t code0 = thread_code(d, r, tpacked | tid);
-#pragma unroll
-        for (int j = 0; j < 2 * P; ++j) {
-          const uint32_t l = tid + NT * j;
-          if (GUARD && l >= tc.amps) break;
-          const R dv = lt[code0 ^ d.jcode[j]].x;
-          const C2 a = tile[l];
-          s += dv * (a.x * a.x + a.y * a.y);
-        }
-      } else if (!GUARD || tid < (tc.amps >> 1)) {
-        const int pivot = d.pivot;
-        const uint32_t xl = d.xl;
-        const uint32_t li0 = insert_zero(tid, pivot);
-        const uint32_t code0 = thread_code(d, r, tpacked | li0);
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-          const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
-          const C2 rq = lt[code0 ^ d.jcode[j]];
-          const C2 a = tile[li], b = tile[lj];
-          // w = conj(a) b ; contribution 2 (R Re w + Q Im w)
-          const R wr = a.x * b.x + a.y * b.y;
-          const R wi = a.x * b.y - a.y * b.x;
-          s += rq.x * wr + rq.y * wi;
-        }
-        s *= 2;
-      }
-      acc_e.add(s);
-    }
+    for (int b = 0; b < nb; ++b) expect_block_any<R, TT, GUARD>(tile, st.bs[b], st, acc_e);
     __syncthreads();
   }
   const double e = block_sum(acc_e.value(), red);
@@ -413,59 +539,66 @@ __global__ void k_reduce_pairs(const double *partial, int nblocks, double *out) 
   }
 }
 
+// ------------------------------------------------------------------ pair enumeration
+
+// Pairs (or diagonal amplitudes) per thread of one group in a 2^TT tile.
+template <int TT, bool GUARD> struct PairShape {
+  static constexpr int P = GUARD ? 1 : (1 << (TT - 1)) / NT;
+};
+
 // ------------------------------------------------------------------ H apply
 
-template <typename R, bool STREAM, int P, bool GUARD>
+template <typename R, bool STREAM, int TT, bool GUARD>
 __global__ void __launch_bounds__(NT, 3) k_happly(const R *psi, R *lam, int n, PassDesc pd,
                                                   const GroupDesc *groups,
                                                   const typename Vec2<R>::type *lut, int first_pass) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
+  constexpr int P = PairShape<TT, GUARD>::P;
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(sizeof(C2), pd, 2, 0);
-  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+  PassDesc pq = pd;
+  pq.b_begin = pq.b_end = 0;
+  const SmemLayout L = smem_layout(sizeof(C2), pq, 2, 0);
+  const Stage<R> st = stage_pass<R>(smem, pq, L, groups, nullptr, lut);
   C2 *tp = reinterpret_cast<C2 *>(smem + L.tiles);
-  C2 *tl = tp + tc.amps;
+  C2 *tl = tp + st.amps;
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   const int ng = pd.g_end - pd.g_begin;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
-    load_tile<R, STREAM>(psi, base, tc, reinterpret_cast<V *>(tp));
+    load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tp));
     if (first_pass) {
-      for (uint32_t l = tid; l < tc.amps; l += NT) tl[l] = C2{0, 0};
+      for (uint32_t l = tid; l < st.amps; l += NT) tl[l] = C2{0, 0};
     } else {
-      load_tile<R, STREAM>(lam, base, tc, reinterpret_cast<V *>(tl));
+      load_tile<R, STREAM>(lam, base, st, reinterpret_cast<V *>(tl));
     }
+    tile_codes(st, ng, t);
     __syncthreads();
-    const uint64_t tpacked = t << pd.T;
     for (int k = 0; k < ng; ++k) {
-      const GroupDesc &d = tc.gs[k];
-      const C2 *lt = tc.lut + d.lut;
-      const int r = d.r;
+      const GroupDesc &d = st.gs[k];
+      const C2 *lt = st.lut + d.lut;
+      const uint32_t code0 = st.tcode[k] ^ d.plane[lane] ^ d.pwarp[warp];
       if (d.kind == KIND_DIAG) {
-        const uint32_t code0 = thread_code(d, r, tpacked | tid);
 #pragma unroll
         for (int j = 0; j < 2 * P; ++j) {
           const uint32_t l = tid + NT * j;
-          if (GUARD && l >= tc.amps) break;
-          const R dv = lt[code0 ^ d.jcode[j]].x;
+          if (GUARD && l >= st.amps) break;
+          const R dv = lt[code0 ^ d.pjcode[j]].x;
           const C2 a = tp[l];
           C2 o = tl[l];
           o.x += dv * a.x;
           o.y += dv * a.y;
           tl[l] = o;
         }
-      } else if (!GUARD || tid < (tc.amps >> 1)) {
-        const int pivot = d.pivot;
+      } else if (!GUARD || tid < (st.amps >> 1)) {
+        const uint32_t li0 = insert_zero(tid, d.pivot);
         const uint32_t xl = d.xl;
-        const uint32_t li0 = insert_zero(tid, pivot);
-        const uint32_t code0 = thread_code(d, r, tpacked | li0);
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
-          const C2 rq = lt[code0 ^ d.jcode[j]];
+          const uint32_t li = li0 | d.pu[j], lj = li ^ xl;
+          const C2 rq = lt[code0 ^ d.pjcode[j]];
           const C2 a = tp[li], b = tp[lj];
           C2 oi = tl[li], oj = tl[lj];
           // lam_i += (R - iQ) psi_j ; lam_j += (R + iQ) psi_i
@@ -479,7 +612,7 @@ __global__ void __launch_bounds__(NT, 3) k_happly(const R *psi, R *lam, int n, P
       }
       __syncthreads();
     }
-    store_tile<R, STREAM>(lam, base, tc, reinterpret_cast<const V *>(tl));
+    store_tile<R, STREAM>(lam, base, st, reinterpret_cast<const V *>(tl));
     __syncthreads();
   }
 }
@@ -518,19 +651,22 @@ __global__ void __launch_bounds__(NT) k_dot(const R *psi, const R *lam, uint64_t
 
 // ------------------------------------------------------------------ reverse sweep
 
-template <typename R, bool STREAM, int P, bool GUARD>
+template <typename R, bool STREAM, int TT, bool GUARD>
 __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDesc pd,
                                                    const GroupDesc *groups,
                                                    const typename Vec2<R>::type *lut,
                                                    const uint64_t *signmask, double *partial) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
+  constexpr int P = PairShape<TT, GUARD>::P;
   extern __shared__ __align__(16) unsigned char smem[];
+  PassDesc pq = pd;
+  pq.b_begin = pq.b_end = 0;
   const SmemLayout L =
-      smem_layout(sizeof(C2), pd, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX);
-  const Tile<R> tc = stage_pass<R>(smem, pd, L, groups, lut);
+      smem_layout(sizeof(C2), pq, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX);
+  const Stage<R> st = stage_pass<R>(smem, pq, L, groups, nullptr, lut);
   C2 *tp = reinterpret_cast<C2 *>(smem + L.tiles);
-  C2 *tl = tp + tc.amps;
+  C2 *tl = tp + st.amps;
   double *acc = reinterpret_cast<double *>(smem + L.extra);   // [RP_MAX]
   R *wpart = reinterpret_cast<R *>(acc + RP_MAX);             // [NT/32][M_MAX]
   const int nrot = pd.rot_end - pd.rot_begin;
@@ -538,20 +674,20 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   const int ng = pd.g_end - pd.g_begin;
-  const uint32_t tid = threadIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
-    load_tile<R, STREAM>(psi, base, tc, reinterpret_cast<V *>(tp));
-    load_tile<R, STREAM>(lam, base, tc, reinterpret_cast<V *>(tl));
+    load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tp));
+    load_tile<R, STREAM>(lam, base, st, reinterpret_cast<V *>(tl));
+    tile_codes(st, ng, t);
     __syncthreads();
-    const uint64_t tpacked = t << pd.T;
     for (int k = ng - 1; k >= 0; --k) {
-      const GroupDesc &d = tc.gs[k];
-      const C2 *lt = tc.lut + d.lut;
-      const int kind = d.kind, r = d.r, m = d.m;
+      const GroupDesc &d = st.gs[k];
+      const C2 *lt = st.lut + d.lut;
+      const int kind = d.kind, m = d.m;
       const int rot0 = (int)d.rot0;
       const uint64_t *sm = signmask + pd.rot_begin + rot0;
+      const uint32_t code0 = st.tcode[k] ^ d.plane[lane] ^ d.pwarp[warp];
       uint64_t mask[M_MAX];
       R a_k[M_MAX];
 #pragma unroll
@@ -560,33 +696,32 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
         a_k[q] = 0;
       }
       if (kind == KIND_DIAG) {
-        const uint32_t code0 = thread_code(d, r, tpacked | tid);
 #pragma unroll
         for (int j = 0; j < 2 * P; ++j) {
           const uint32_t l = tid + NT * j;
-          if (GUARD && l >= tc.amps) break;
-          const uint32_t code = code0 ^ d.jcode[j];
+          if (GUARD && l >= st.amps) break;
+          const uint32_t code = code0 ^ d.pjcode[j];
           const C2 cs = lt[code];
           const C2 a = tp[l], b = tl[l];
           const R val = b.x * a.y - b.y * a.x;   // Im(conj(lam) psi)
 #pragma unroll
           for (int q = 0; q < M_MAX; ++q)
             if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
-          const R c = cs.x, s = -cs.y;
-          tp[l] = C2{c * a.x + s * a.y, c * a.y - s * a.x};
-          tl[l] = C2{c * b.x + s * b.y, c * b.y - s * b.x};
+          C2 a2 = a, b2 = b;
+          phase(a2, cs.x, -cs.y);
+          phase(b2, cs.x, -cs.y);
+          tp[l] = a2;
+          tl[l] = b2;
         }
-      } else if (!GUARD || tid < (tc.amps >> 1)) {
-        const int pivot = d.pivot;
+      } else if (!GUARD || tid < (st.amps >> 1)) {
+        const uint32_t li0 = insert_zero(tid, d.pivot);
         const uint32_t xl = d.xl;
-        const uint32_t li0 = insert_zero(tid, pivot);
-        const uint32_t code0 = thread_code(d, r, tpacked | li0);
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          const uint32_t li = li0 | insert_zero((uint32_t)(NT * j), pivot), lj = li ^ xl;
-          const uint32_t code = code0 ^ d.jcode[j];
+          const uint32_t li = li0 | d.pu[j], lj = li ^ xl;
+          const uint32_t code = code0 ^ d.pjcode[j];
           const C2 cs = lt[code];
-          const C2 pa = tp[li], pb = tp[lj], la = tl[li], lb = tl[lj];
+          C2 pa = tp[li], pb = tp[lj], la = tl[li], lb = tl[lj];
           R val;
           if (kind == KIND_REAL) {
             // Re(conj(lam_j) psi_i - conj(lam_i) psi_j)
@@ -598,18 +733,17 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
 #pragma unroll
           for (int q = 0; q < M_MAX; ++q)
             if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
-          const R c = cs.x, s = -cs.y;
           if (kind == KIND_REAL) {
-            tp[li] = C2{c * pa.x - s * pb.x, c * pa.y - s * pb.y};
-            tp[lj] = C2{s * pa.x + c * pb.x, s * pa.y + c * pb.y};
-            tl[li] = C2{c * la.x - s * lb.x, c * la.y - s * lb.y};
-            tl[lj] = C2{s * la.x + c * lb.x, s * la.y + c * lb.y};
+            rot_real(pa, pb, cs.x, -cs.y);
+            rot_real(la, lb, cs.x, -cs.y);
           } else {
-            tp[li] = C2{c * pa.x + s * pb.y, c * pa.y - s * pb.x};
-            tp[lj] = C2{c * pb.x + s * pa.y, c * pb.y - s * pa.x};
-            tl[li] = C2{c * la.x + s * lb.y, c * la.y - s * lb.x};
-            tl[lj] = C2{c * lb.x + s * la.y, c * lb.y - s * la.x};
+            rot_xrot(pa, pb, cs.x, -cs.y);
+            rot_xrot(la, lb, cs.x, -cs.y);
           }
+          tp[li] = pa;
+          tp[lj] = pb;
+          tl[li] = la;
+          tl[lj] = lb;
         }
       }
       // warp sums -> smem -> fixed-order CTA sum into acc (double)
@@ -629,8 +763,8 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
       }
       __syncthreads();
     }
-    store_tile<R, STREAM>(psi, base, tc, reinterpret_cast<const V *>(tp));
-    store_tile<R, STREAM>(lam, base, tc, reinterpret_cast<const V *>(tl));
+    store_tile<R, STREAM>(psi, base, st, reinterpret_cast<const V *>(tp));
+    store_tile<R, STREAM>(lam, base, st, reinterpret_cast<const V *>(tl));
     __syncthreads();
   }
   for (int k = threadIdx.x; k < nrot; k += NT) partial[(size_t)blockIdx.x * RP_MAX + k] = acc[k];
@@ -681,39 +815,41 @@ unsigned grid_for(uint64_t ntiles, int per_sm) {
 
 bool streaming(int n, int bytes) { return ((uint64_t)bytes << n) > (64ull << 20); }
 
-// Pick the kernel instantiation for a pass: P = 2^(T-1) / NT pairs per thread.
-#define Q2_DISPATCH(KERNEL, R, n, T, ...)                                              \
-  [&]() -> decltype(&KERNEL<R, true, 1, true>) {                                     \
-    const bool st_ = streaming(n, 2 * (int)sizeof(R));                               \
-    switch (T) {                                                                       \
-      case 9: return st_ ? &KERNEL<R, true, 1, false> : &KERNEL<R, false, 1, false>;  \
-      case 10: return st_ ? &KERNEL<R, true, 2, false> : &KERNEL<R, false, 2, false>; \
-      case 11: return st_ ? &KERNEL<R, true, 4, false> : &KERNEL<R, false, 4, false>; \
-      case 12: return st_ ? &KERNEL<R, true, 8, false> : &KERNEL<R, false, 8, false>; \
-      case 13: return st_ ? &KERNEL<R, true, 16, false> : &KERNEL<R, false, 16, false>; \
-      default: return st_ ? &KERNEL<R, true, 1, true> : &KERNEL<R, false, 1, true>;   \
-    }                                                                                  \
+// Pick the kernel instantiation for a pass's tile size T (9..13; smaller tiles are guarded).
+#define Q2_DISPATCH(KERNEL, R, n, T)                                                      \
+  [&]() -> decltype(&KERNEL<R, true, 9, true>) {                                        \
+    const bool st_ = streaming(n, 2 * (int)sizeof(R));                                  \
+    switch (T) {                                                                          \
+      case 9: return st_ ? &KERNEL<R, true, 9, false> : &KERNEL<R, false, 9, false>;     \
+      case 10: return st_ ? &KERNEL<R, true, 10, false> : &KERNEL<R, false, 10, false>;  \
+      case 11: return st_ ? &KERNEL<R, true, 11, false> : &KERNEL<R, false, 11, false>;  \
+      case 12: return st_ ? &KERNEL<R, true, 12, false> : &KERNEL<R, false, 12, false>;  \
+      case 13: return st_ ? &KERNEL<R, true, 13, false> : &KERNEL<R, false, 13, false>;  \
+      default: return st_ ? &KERNEL<R, true, 9, true> : &KERNEL<R, false, 9, true>;      \
+    }                                                                                     \
   }()
+
+PassDesc worst_pass(int T, int C) {
+  PassDesc pd{};
+  pd.T = T;
+  pd.C = C;
+  pd.g_begin = 0;
+  pd.g_end = G_STAGE;
+  pd.b_begin = 0;
+  pd.b_end = G_STAGE;
+  pd.lut_count = LUT_STAGE;
+  return pd;
+}
 
 }  // namespace
 
 size_t tile_smem_bytes(int amp_bytes, int T, int C, int vectors) {
-  PassDesc pd{};
-  pd.T = T;
-  pd.C = C;
-  pd.g_begin = 0;
-  pd.g_end = G_STAGE;
-  pd.lut_count = LUT_STAGE;
-  return smem_layout(amp_bytes, pd, vectors, sizeof(double) * (NT / 32)).total;
+  return smem_layout(amp_bytes, worst_pass(T, C), vectors, sizeof(double) * (NT / 32)).total;
 }
 
 size_t reverse_smem_bytes(int amp_bytes, int T, int C) {
-  PassDesc pd{};
-  pd.T = T;
-  pd.C = C;
-  pd.g_begin = 0;
-  pd.g_end = G_STAGE;
-  pd.lut_count = LUT_STAGE;
+  PassDesc pd = worst_pass(T, C);
+  pd.b_end = 0;
   return smem_layout(amp_bytes, pd, 2, sizeof(double) * RP_MAX + (size_t)(amp_bytes / 2) * (NT / 32) * M_MAX)
       .total;
 }
@@ -736,15 +872,15 @@ cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups, const void *lut,
-                         bool inverse, cudaStream_t st) {
+cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
+                         const BlockDesc *blocks, const void *lut, bool inverse, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const size_t smem = smem_layout(sizeof(C2), pd, 1, 0).total;
   auto k = Q2_DISPATCH(k_sweep, R, n, pd.T);
   cudaError_t e = prepare(k, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
-  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), inverse ? 1 : 0);
+  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), inverse ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -759,13 +895,15 @@ int expect_grid(int n, int T, int C) {
 
 template <typename R>
 cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                          const void *lut, double *partial, int grid, bool first, cudaStream_t st) {
+                          const BlockDesc *blocks, const void *lut, double *partial, int grid, bool first,
+                          cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const size_t smem = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32)).total;
   auto k = Q2_DISPATCH(k_expect, R, n, pd.T);
   cudaError_t e = prepare(k, smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, reinterpret_cast<const C2 *>(lut), partial, first ? 1 : 0);
+  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), partial,
+                            first ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -778,7 +916,9 @@ template <typename R>
 cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
                           const void *lut, bool first, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
-  const size_t smem = smem_layout(sizeof(C2), pd, 2, 0).total;
+  PassDesc pq = pd;
+  pq.b_begin = pq.b_end = 0;
+  const size_t smem = smem_layout(sizeof(C2), pq, 2, 0).total;
   auto k = Q2_DISPATCH(k_happly, R, n, pd.T);
   cudaError_t e = prepare(k, smem);
   if (e != cudaSuccess) return e;
@@ -802,21 +942,14 @@ cudaError_t launch_dot(const R *psi, const R *lam, int n, double *partial, int g
 }
 
 template <typename R>
-int reverse_grid(int n, int T, int C) {
-  using C2 = typename Vec2<R>::type;
-  const size_t smem = reverse_smem_bytes(sizeof(C2), T, C);
-  auto k = Q2_DISPATCH(k_reverse, R, n, T);
-  prepare(k, smem);
-  return (int)grid_for(1ull << (n - T), blocks_per_sm(k, smem));
-}
-
-template <typename R>
 cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
                            const void *lut, const uint64_t *signmask, double *partial, double *gphi,
                            cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
+  PassDesc pq = pd;
+  pq.b_begin = pq.b_end = 0;
   const size_t smem =
-      smem_layout(sizeof(C2), pd, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX).total;
+      smem_layout(sizeof(C2), pq, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX).total;
   auto k = Q2_DISPATCH(k_reverse, R, n, pd.T);
   cudaError_t e = prepare(k, smem);
   if (e != cudaSuccess) return e;
@@ -830,16 +963,16 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
 
 #define Q2_INST(R)                                                                                  \
   template cudaError_t launch_init_hf<R>(R *, int, int, cudaStream_t);                             \
-  template cudaError_t launch_sweep<R>(R *, int, const PassDesc &, const GroupDesc *, const void *, \
-                                       bool, cudaStream_t);                                         \
+  template cudaError_t launch_sweep<R>(R *, int, const PassDesc &, const GroupDesc *,              \
+                                       const BlockDesc *, const void *, bool, cudaStream_t);        \
   template int expect_grid<R>(int, int, int);                                                       \
   template cudaError_t launch_expect<R>(const R *, int, const PassDesc &, const GroupDesc *,        \
-                                        const void *, double *, int, bool, cudaStream_t);           \
+                                        const BlockDesc *, const void *, double *, int, bool,       \
+                                        cudaStream_t);                                              \
   template cudaError_t launch_happly<R>(const R *, R *, int, const PassDesc &, const GroupDesc *,   \
                                         const void *, bool, cudaStream_t);                          \
   template int dot_grid<R>(int);                                                                    \
   template cudaError_t launch_dot<R>(const R *, const R *, int, double *, int, cudaStream_t);       \
-  template int reverse_grid<R>(int, int, int);                                                      \
   template cudaError_t launch_reverse<R>(R *, R *, int, const PassDesc &, const GroupDesc *,        \
                                          const void *, const uint64_t *, double *, double *,        \
                                          cudaStream_t);

@@ -14,19 +14,19 @@ cudaError_t launch_reduce_pairs(const double *partial, int nblocks, double *out,
 
 template <typename R> cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st);
 template <typename R>
-cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups, const void *lut,
-                         bool inverse, cudaStream_t st);
+cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
+                         const BlockDesc *blocks, const void *lut, bool inverse, cudaStream_t st);
 template <typename R> int expect_grid(int n, int T, int C);
 template <typename R>
 cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                          const void *lut, double *partial, int grid, bool first, cudaStream_t st);
+                          const BlockDesc *blocks, const void *lut, double *partial, int grid, bool first,
+                          cudaStream_t st);
 template <typename R>
 cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
                           const void *lut, bool first, cudaStream_t st);
 template <typename R> int dot_grid(int n);
 template <typename R>
 cudaError_t launch_dot(const R *psi, const R *lam, int n, double *partial, int grid, cudaStream_t st);
-template <typename R> int reverse_grid(int n, int T, int C);
 template <typename R>
 cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
                            const void *lut, const uint64_t *signmask, double *partial, double *gphi,

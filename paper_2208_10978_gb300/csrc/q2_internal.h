@@ -38,7 +38,7 @@ constexpr int NT = 256;          // threads per CTA of the tile kernels
 constexpr int R_MAX = 8;         // max code bits of a Hamiltonian group
 constexpr int R_MAX_ROT = 6;     // max code bits of a rotation group (sign masks fit 64 bits)
 constexpr int M_MAX = 16;        // max rotations in one rotation group
-constexpr int P_MAX = 32;        // max per-thread iterations over a tile (2^T <= NT * P_MAX)
+constexpr int P_MAX = 32;        // max per-thread diagonal iterations over a tile (2^T <= NT * P_MAX)
 constexpr int RP_MAX = 512;      // max rotations in one pass (reverse-sweep partials)
 constexpr int G_STAGE = 64;      // max groups per pass (staged in shared memory)
 constexpr int LUT_STAGE = 1024;  // max LUT entries per pass (staged in shared memory)
@@ -47,19 +47,55 @@ constexpr int T_LIMIT = 13;
 
 enum : uint8_t { KIND_DIAG = 0, KIND_REAL = 1, KIND_XROT = 2, KIND_PAIR = 3 };
 
-// One group as the kernels read it (uniform across a CTA, read through L1).
+constexpr int D_MAX = 4;         // max span dimension of a register block (rotations)
+constexpr int D_MAX_EXPECT = 3;  // max span dimension of a Hamiltonian register block
+
+// Register blocks.  Consecutive groups of a pass whose xmasks span d <= D_MAX
+// local dimensions form a block.  The block's span V (basis v_1..v_d in
+// reduced echelon form, pivots = highest bits) splits a tile into 2^(T-d)
+// cosets; thread tid takes cosets s = tid + NT*j, whose amplitudes are the
+// local indices base(s) ^ comb[c] (c < 2^d), base(s) = s with zero bits
+// inserted at the pivots.  A thread keeps one coset in registers while it
+// applies every group of the block; a group with xmask coordinates a in V
+// pairs combo c with c ^ a.  The code of an amplitude is the XOR of a tile
+// part (computed once per tile) and host-tabulated parts for the lane, the
+// warp, the coset j and the combo c, all linear in the local index.
 struct alignas(16) GroupDesc {
-  uint64_t bp[R_MAX];     // code basis in packed-index space
-  uint32_t xl;            // xmask in local-index space (0 for diagonal groups)
-  uint32_t lut;           // first LUT entry of this group
-  uint32_t rot0;          // rotation groups: first rotation, relative to the pass
-  uint8_t kind;           // KIND_*
-  uint8_t pivot;          // local bit removed to enumerate pairs (highest bit of xl)
-  uint8_t r;              // code bits; the LUT has 2^r entries
-  uint8_t m;              // rotation groups: number of rotations
-  uint8_t jcode[P_MAX];   // code of the j-th per-thread offset (NT * j, pivot-inserted)
+  uint64_t bp[R_MAX];      // code basis in packed-index space
+  uint32_t xl;             // xmask in local-index space (0 for diagonal groups)
+  uint32_t lut;            // first LUT entry of this group
+  uint32_t rot0;           // rotation groups: first rotation, relative to the pass
+  uint8_t kind;            // KIND_*
+  uint8_t r;               // code bits; the LUT has 2^r entries
+  uint8_t m;               // rotation groups: number of rotations
+  uint8_t a;               // xmask coordinates in its block's basis (0: diagonal)
+  // block enumeration (sweep, expectation)
+  uint8_t bjcode[16];      // code of coset offset uj[j]
+  uint8_t bccode[16];      // code of combo offset comb[c]
+  uint8_t blane[32];       // code of base(lane)
+  uint8_t bwarp[8];        // code of base(32 * warp)
+  // pair enumeration (H apply, reverse sweep): pair q = tid + NT*j is local
+  // index insert_zero(q, pivot), partner ^ xl; diagonal groups use l = tid + NT*j
+  uint8_t pivot;           // highest bit of xl
+  uint8_t pad0[7];
+  uint8_t pjcode[32];      // code of the j-th per-thread offset
+  uint8_t plane[32];       // code of the lane part of the thread's first element
+  uint8_t pwarp[8];        // code of the warp part
+  uint16_t pu[16];         // local offset of pair j for thread 0: insert_zero(NT*j, pivot)
+  uint8_t pad1[8];
 };
-static_assert(sizeof(GroupDesc) == 112, "GroupDesc layout");
+static_assert(sizeof(GroupDesc) == 272, "GroupDesc layout");
+
+struct alignas(16) BlockDesc {
+  uint16_t comb[16];       // local offset of combo c (c < 2^d)
+  uint16_t uj[16];         // local offset of coset j for thread 0: base(NT * j)
+  uint8_t d;               // span dimension, 1..D_MAX
+  uint8_t piv[D_MAX];      // pivots, ascending
+  uint8_t pad0[3];
+  uint16_t g_begin, g_end; // groups of the block, relative to the pass
+  uint8_t pad1[4];
+};
+static_assert(sizeof(BlockDesc) == 80, "BlockDesc layout");
 
 struct PassDesc {
   uint64_t w[T_LIMIT];    // local basis; w[b] = e_b for b < C
@@ -69,6 +105,7 @@ struct PassDesc {
   int g_begin, g_end;     // groups [g_begin, g_end)
   int rot_begin, rot_end; // rotation plans: rotations covered by this pass
   int lut_begin, lut_count;  // LUT entries of this pass's groups (contiguous)
+  int b_begin, b_end;     // register blocks [b_begin, b_end)
 };
 
 // Host-side schedule of a rotation list (an ansatz or one apply call).
@@ -77,6 +114,7 @@ struct RotPlan {
   int T = 0;
   std::vector<PassDesc> passes;
   std::vector<GroupDesc> groups;       // device image
+  std::vector<BlockDesc> blocks;
   std::vector<int> grp_rot_begin;      // rotations of group g: [begin, begin + m)
   std::vector<uint8_t> rot_coord;      // per rotation: z_k in the group's code basis
   std::vector<int8_t> rot_sigma;       // per rotation: fixed sign of its angle in the LUT
@@ -93,6 +131,7 @@ struct HamPlan {
   int T = 0;
   std::vector<PassDesc> passes;
   std::vector<GroupDesc> groups;
+  std::vector<BlockDesc> blocks;
   std::vector<double> lut2;            // (R, Q) per group and code
   int64_t lut_entries = 0;
 };

@@ -129,7 +129,16 @@ Tiling make_tiling(int n, int T, int Cmin, const std::vector<uint64_t> &gens) {
   return t;
 }
 
-// Device descriptor of one group inside a pass.
+// Code of a local index for a group: bits parity(l & bp_k), local part only.
+uint32_t local_code(const GroupDesc &d, uint64_t l, int T) {
+  const uint64_t lm = (1ull << T) - 1;
+  uint32_t c = 0;
+  for (int k = 0; k < d.r; ++k) c |= (uint32_t)parity64(l & d.bp[k] & lm) << k;
+  return c;
+}
+
+// Device descriptor of one group inside a pass (pair-enumeration tables
+// included; block tables are filled by form_blocks).
 GroupDesc make_desc(const RawGroup &g, const Tiling &tl, uint32_t lut_off) {
   GroupDesc d;
   std::memset(&d, 0, sizeof(d));
@@ -143,17 +152,123 @@ GroupDesc make_desc(const RawGroup &g, const Tiling &tl, uint32_t lut_off) {
   d.pivot = diag ? 0 : (uint8_t)high_bit(d.xl);
   const int64_t per_tile = diag ? (1ll << T) : (1ll << (T - 1));
   const int64_t P = std::max<int64_t>(1, per_tile / NT);
-  if (P > P_MAX) throw std::logic_error("tile too large for the per-thread offset table");
-  const uint64_t local_mask = (1ull << T) - 1;
+  if (P > P_MAX || (!diag && P > 16)) throw std::logic_error("tile too large for the per-thread tables");
   for (int64_t j = 0; j < P; ++j) {
     uint32_t v = (uint32_t)(NT * j);
-    if (!diag) v = insert_zero(v, d.pivot);
-    uint32_t code = 0;
-    for (int l = 0; l < d.r; ++l) code |= (uint32_t)parity64(v & d.bp[l] & local_mask) << l;
-    d.jcode[j] = (uint8_t)code;
+    if (!diag) {
+      v = insert_zero(v, d.pivot);
+      d.pu[j] = (uint16_t)v;
+    }
+    d.pjcode[j] = (uint8_t)local_code(d, v, T);
+  }
+  for (int lane = 0; lane < 32; ++lane) {
+    const uint32_t v = diag ? (uint32_t)lane : insert_zero((uint32_t)lane, d.pivot);
+    d.plane[lane] = (uint8_t)local_code(d, v, T);
+  }
+  for (int w = 0; w < NT / 32; ++w) {
+    const uint32_t v = diag ? (uint32_t)(32 * w) : insert_zero((uint32_t)(32 * w), d.pivot);
+    d.pwarp[w] = (uint8_t)local_code(d, v, T);
   }
   return d;
 }
+
+// base(s): s with zero bits inserted at the (ascending) pivots.
+uint32_t block_base(uint32_t s, const BlockDesc &b) {
+  for (int i = 0; i < b.d; ++i) s = insert_zero(s, b.piv[i]);
+  return s;
+}
+
+// Partition groups[first, last) of a pass into register blocks of span <= dmax.
+// With reorder, groups are first arranged greedily so that blocks stay small
+// (allowed for Hamiltonian terms, whose sum is order-free).
+void form_blocks(std::vector<GroupDesc> &groups, size_t first, size_t last, int T, int dmax,
+                 bool reorder, std::vector<BlockDesc> &blocks) {
+  if (reorder) {
+    std::vector<GroupDesc> rest(groups.begin() + first, groups.begin() + last), out;
+    std::vector<char> used(rest.size(), 0);
+    size_t left = rest.size();
+    while (left) {
+      Gf2Basis span;
+      for (;;) {
+        size_t best = rest.size();
+        int best_add = 99;
+        for (size_t i = 0; i < rest.size(); ++i) {
+          if (used[i]) continue;
+          const uint64_t xl = rest[i].xl;
+          const int add = (xl == 0 || span.contains(xl)) ? 0 : 1;
+          if (span.rank() + add > dmax) continue;
+          if (add < best_add) {
+            best = i;
+            best_add = add;
+            if (add == 0) break;
+          }
+        }
+        if (best == rest.size()) break;
+        used[best] = 1;
+        --left;
+        if (rest[best].xl) span.add(rest[best].xl);
+        out.push_back(rest[best]);
+      }
+    }
+    std::copy(out.begin(), out.end(), groups.begin() + first);
+  }
+  size_t g = first;
+  while (g < last) {
+    Gf2Basis span;
+    size_t e = g;
+    while (e < last) {
+      const uint64_t xl = groups[e].xl;
+      if (xl && !span.contains(xl) && span.rank() >= dmax) break;
+      if (xl) span.add(xl);
+      ++e;
+    }
+    // reduced echelon basis of the span (pivot = highest bit, no other pivot bits)
+    std::vector<uint64_t> v = span.red;   // distinct highest bits
+    if (v.empty()) v.push_back(1);        // diagonal-only block: any one local direction
+    std::sort(v.begin(), v.end(), [](uint64_t a, uint64_t b) { return high_bit(a) < high_bit(b); });
+    // clear every pivot from the other rows, lowest pivot first (no bit comes back)
+    for (size_t i = 0; i < v.size(); ++i)
+      for (size_t k = 0; k < v.size(); ++k)
+        if (k != i && ((v[k] >> high_bit(v[i])) & 1)) v[k] ^= v[i];
+    BlockDesc b;
+    std::memset(&b, 0, sizeof(b));
+    b.d = (uint8_t)v.size();
+    for (int i = 0; i < b.d; ++i) b.piv[i] = (uint8_t)high_bit(v[i]);
+    for (uint32_t c = 0; c < (1u << b.d); ++c) {
+      uint64_t o = 0;
+      for (int i = 0; i < b.d; ++i)
+        if ((c >> i) & 1) o ^= v[i];
+      b.comb[c] = (uint16_t)o;
+    }
+    const int64_t ncos = 1ll << (T - b.d);
+    const int64_t J = std::max<int64_t>(1, ncos / NT);
+    if (J > 16) throw std::logic_error("too many cosets per thread");
+    for (int64_t j = 0; j < J; ++j) b.uj[j] = (uint16_t)block_base((uint32_t)(NT * j), b);
+    b.g_begin = (uint16_t)(g - first);
+    b.g_end = (uint16_t)(e - first);
+    for (size_t k = g; k < e; ++k) {
+      GroupDesc &d = groups[k];
+      // coordinates of xl in the basis v (v is in reduced echelon form)
+      uint32_t a = 0;
+      uint64_t rem = d.xl;
+      for (int i = b.d - 1; i >= 0; --i)
+        if ((rem >> b.piv[i]) & 1) {
+          rem ^= v[i];
+          a |= 1u << i;
+        }
+      if (rem != 0) throw std::logic_error("group xmask outside its block span");
+      d.a = (uint8_t)a;
+      for (uint32_t c = 0; c < (1u << b.d); ++c) d.bccode[c] = (uint8_t)local_code(d, b.comb[c], T);
+      for (int64_t j = 0; j < J; ++j) d.bjcode[j] = (uint8_t)local_code(d, b.uj[j], T);
+      for (int lane = 0; lane < 32; ++lane) d.blane[lane] = (uint8_t)local_code(d, block_base(lane, b), T);
+      for (int w = 0; w < NT / 32; ++w) d.bwarp[w] = (uint8_t)local_code(d, block_base(32 * w, b), T);
+    }
+    blocks.push_back(b);
+    g = e;
+  }
+}
+
+int block_dmax(int T, int cap = D_MAX) { return std::max(1, std::min(cap, T - 8)); }
 
 PassDesc make_pass(const Tiling &tl) {
   PassDesc pd;
@@ -278,6 +393,9 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
     pd.g_end = (int)P.groups.size();
     pd.lut_begin = (int)P.groups[pd.g_begin].lut;
     pd.lut_count = (int)lut - pd.lut_begin;
+    pd.b_begin = (int)P.blocks.size();
+    form_blocks(P.groups, pd.g_begin, pd.g_end, T, block_dmax(T), false, P.blocks);
+    pd.b_end = (int)P.blocks.size();
     pd.rot_end = (int)(groups[pr.ge - 1].members.back() + 1);
     P.max_pass_rots = std::max(P.max_pass_rots, pd.rot_end - pd.rot_begin);
     P.passes.push_back(pd);
@@ -472,6 +590,9 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
     pd.g_end = (int)H.groups.size();
     pd.lut_begin = (int)H.groups[pd.g_begin].lut;
     pd.lut_count = (int)lut - pd.lut_begin;
+    pd.b_begin = (int)H.blocks.size();
+    form_blocks(H.groups, pd.g_begin, pd.g_end, T, block_dmax(T, D_MAX_EXPECT), true, H.blocks);
+    pd.b_end = (int)H.blocks.size();
     H.passes.push_back(pd);
   }
   H.lut_entries = lut;

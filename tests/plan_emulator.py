@@ -1,11 +1,19 @@
-"""Host-side walk of the library's pass/group tables (test helper).
+"""Host-side walk of the library's pass/group/block tables (test helper).
 
 Reads the schedules exported by include/q2_debug.h and applies them to a
-NumPy state exactly the way the tile kernels index memory: tile t, local
-index l -> amplitude deposit(t, umask) ^ XOR_b(l_b w_b); thread tid handles
-pair q = tid + NT * j with code = code(tile, tid) ^ jcode[j].  Comparing the
-result with the oracle checks the schedulers (tiling bases, codes, LUTs,
-sign masks) on the CPU; the CUDA kernels themselves are checked on the GPU.
+NumPy state exactly the way the tile kernels index memory:
+
+* tile t, local index l -> amplitude deposit(t, umask) ^ XOR_b(l_b w_b);
+* sweep and expectation walk register blocks: thread tid, coset j holds the
+  local indices base(tid) ^ uj[j] ^ comb[c]; a group pairs combo c with c ^ a;
+  code = tilecode ^ blane[lane] ^ bwarp[warp] ^ bjcode[j] ^ bccode[c];
+* H apply and the reverse sweep walk groups one at a time: pair j of thread
+  tid is insert_zero(tid, pivot) | pu[j] (diagonal: tid + NT*j);
+  code = tilecode ^ plane[lane] ^ pwarp[warp] ^ pjcode[j].
+
+Comparing the result with the oracle checks the schedulers (tiling bases,
+blocks, codes, LUTs, sign masks) on the CPU; the CUDA kernels themselves are
+checked on the GPU.
 """
 
 import ctypes
@@ -14,10 +22,15 @@ import numpy as np
 
 PASS_DT = np.dtype([("w", "<u8", 13), ("umask", "<u8"), ("T", "<i4"), ("C", "<i4"),
                     ("g_begin", "<i4"), ("g_end", "<i4"), ("rot_begin", "<i4"), ("rot_end", "<i4"),
-                    ("lut_begin", "<i4"), ("lut_count", "<i4")])
+                    ("lut_begin", "<i4"), ("lut_count", "<i4"), ("b_begin", "<i4"), ("b_end", "<i4")])
 GROUP_DT = np.dtype([("bp", "<u8", 8), ("xl", "<u4"), ("lut", "<u4"), ("rot0", "<u4"), ("kind", "u1"),
-                     ("pivot", "u1"), ("r", "u1"), ("m", "u1"), ("jcode", "u1", 32)])
-assert PASS_DT.itemsize == 144 and GROUP_DT.itemsize == 112
+                     ("r", "u1"), ("m", "u1"), ("a", "u1"), ("bjcode", "u1", 16), ("bccode", "u1", 16),
+                     ("blane", "u1", 32), ("bwarp", "u1", 8), ("pivot", "u1"), ("pad0", "u1", 7),
+                     ("pjcode", "u1", 32), ("plane", "u1", 32), ("pwarp", "u1", 8), ("pu", "<u2", 16),
+                     ("pad1", "u1", 8)])
+BLOCK_DT = np.dtype([("comb", "<u2", 16), ("uj", "<u2", 16), ("d", "u1"), ("piv", "u1", 4), ("pad0", "u1", 3),
+                     ("g_begin", "<u2"), ("g_end", "<u2"), ("pad1", "u1", 4)])
+assert PASS_DT.itemsize == 152 and GROUP_DT.itemsize == 272 and BLOCK_DT.itemsize == 80
 
 DIAG, REAL, XROT, PAIR = 0, 1, 2, 3
 
@@ -30,33 +43,37 @@ def rot_plan(lib, n, x, z, phi, T, C):
     x = np.ascontiguousarray(x, dtype=np.uint64)
     z = np.ascontiguousarray(z, dtype=np.uint64)
     phi = np.ascontiguousarray(phi, dtype=np.float64)
-    counts = np.zeros(3, dtype=np.int64)
+    counts = np.zeros(4, dtype=np.int64)
     f = lib.q2_debug_rot_plan
-    f.argtypes = [ctypes.c_int, ctypes.c_int64] + [ctypes.c_void_p] * 3 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 5
+    f.argtypes = [ctypes.c_int, ctypes.c_int64] + [ctypes.c_void_p] * 3 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 6
     f.restype = ctypes.c_int
-    assert f(n, len(x), _p(x), _p(z), _p(phi), T, C, _p(counts), None, None, None, None) == 0
+    assert f(n, len(x), _p(x), _p(z), _p(phi), T, C, _p(counts), None, None, None, None, None) == 0
     passes = np.zeros(counts[0], dtype=PASS_DT)
     groups = np.zeros(counts[1], dtype=GROUP_DT)
+    blocks = np.zeros(counts[3], dtype=BLOCK_DT)
     lut = np.zeros(2 * max(1, counts[2]))
     sm = np.zeros(max(1, len(x)), dtype=np.uint64)
-    assert f(n, len(x), _p(x), _p(z), _p(phi), T, C, _p(counts), _p(passes), _p(groups), _p(lut), _p(sm)) == 0
-    return passes, groups, lut.reshape(-1, 2), sm
+    assert f(n, len(x), _p(x), _p(z), _p(phi), T, C, _p(counts), _p(passes), _p(groups), _p(blocks),
+             _p(lut), _p(sm)) == 0
+    return passes, groups, blocks, lut.reshape(-1, 2), sm
 
 
 def ham_plan(lib, n, x, z, c, T, C):
     x = np.ascontiguousarray(x, dtype=np.uint64)
     z = np.ascontiguousarray(z, dtype=np.uint64)
     c = np.ascontiguousarray(c, dtype=np.float64)
-    counts = np.zeros(3, dtype=np.int64)
+    counts = np.zeros(4, dtype=np.int64)
     f = lib.q2_debug_ham_plan
-    f.argtypes = [ctypes.c_int, ctypes.c_int64] + [ctypes.c_void_p] * 3 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 4
+    f.argtypes = [ctypes.c_int, ctypes.c_int64] + [ctypes.c_void_p] * 3 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 5
     f.restype = ctypes.c_int
-    assert f(n, len(x), _p(x), _p(z), _p(c), T, C, _p(counts), None, None, None) == 0
+    assert f(n, len(x), _p(x), _p(z), _p(c), T, C, _p(counts), None, None, None, None) == 0
     passes = np.zeros(counts[0], dtype=PASS_DT)
     groups = np.zeros(counts[1], dtype=GROUP_DT)
+    blocks = np.zeros(counts[3], dtype=BLOCK_DT)
     lut = np.zeros(2 * max(1, counts[2]))
-    assert f(n, len(x), _p(x), _p(z), _p(c), T, C, _p(counts), _p(passes), _p(groups), _p(lut)) == 0
-    return passes, groups, lut.reshape(-1, 2)
+    assert f(n, len(x), _p(x), _p(z), _p(c), T, C, _p(counts), _p(passes), _p(groups), _p(blocks),
+             _p(lut)) == 0
+    return passes, groups, blocks, lut.reshape(-1, 2)
 
 
 def _par(a):
@@ -93,29 +110,45 @@ def tile_index(n, pd):
     return (base[:, None] ^ off[l >> np.uint64(C)][None, :]) | (l & np.uint64((1 << C) - 1))[None, :]
 
 
-def _codes(g, T, ntiles, nt, pair):
-    """code[t, tid, j] as the kernels form it."""
-    tid = np.arange(nt, dtype=np.uint64)
-    lt = _insert0(tid, int(g["pivot"])) if pair else tid
-    packed = (np.arange(ntiles, dtype=np.uint64)[:, None] << np.uint64(T)) | lt[None, :]
-    code0 = np.zeros(packed.shape, dtype=np.int64)
-    for l in range(int(g["r"])):
-        code0 |= _par(packed & np.uint64(g["bp"][l])) << l
-    return code0
+def _tilecode(g, T, ntiles):
+    t = np.arange(ntiles, dtype=np.uint64) << np.uint64(T)
+    c = np.zeros(ntiles, dtype=np.int64)
+    for k in range(int(g["r"])):
+        c |= _par(t & np.uint64(g["bp"][k])) << k
+    return c
 
 
-def _layout(g, T, NT, pair):
-    per = 1 << (T - 1) if pair else 1 << T
-    P = max(1, per // NT)
-    nt = min(NT, per)
-    tid = np.arange(nt, dtype=np.uint64)
-    j = np.arange(P, dtype=np.uint64)
-    q = tid[:, None] + np.uint64(NT) * j[None, :]
-    li = _insert0(q, int(g["pivot"])) if pair else q
-    return P, nt, li.astype(np.int64)
+def _block_layout(b, T, NT):
+    """Local indices [nthr, J, 2^d] of every thread's cosets and their (lane, warp)."""
+    d = int(b["d"])
+    ncos = 1 << (T - d)
+    J = max(1, ncos // NT)
+    nthr = min(NT, ncos)
+    tid = np.arange(nthr, dtype=np.uint64)
+    base = tid.copy()
+    for i in range(d):
+        base = _insert0(base, int(b["piv"][i]))
+    l = (base[:, None, None] ^ b["uj"][:J].astype(np.uint64)[None, :, None]
+         ^ b["comb"][:1 << d].astype(np.uint64)[None, None, :])
+    return d, J, nthr, l.astype(np.int64), (tid % 32).astype(np.int64), (tid // 32).astype(np.int64)
 
 
-def sweep(psi, n, passes, groups, lut, NT, inverse=False):
+def _block_codes(g, d, J, lane, warp, tcode):
+    """code[t, tid, j, c]."""
+    th = (g["blane"][lane].astype(np.int64) ^ g["bwarp"][warp].astype(np.int64))
+    return (tcode[:, None, None, None] ^ th[None, :, None, None]
+            ^ g["bjcode"][:J].astype(np.int64)[None, None, :, None]
+            ^ g["bccode"][:1 << d].astype(np.int64)[None, None, None, :])
+
+
+def _pair_combos(a, d):
+    """Combos c with the highest set bit of a clear, and their partners c ^ a."""
+    hb = a.bit_length() - 1
+    cs = np.array([c for c in range(1 << d) if not (c >> hb) & 1], dtype=np.int64)
+    return cs, cs ^ a
+
+
+def sweep(psi, n, passes, groups, blocks, lut, NT, inverse=False):
     psi = psi.copy()
     order = range(len(passes) - 1, -1, -1) if inverse else range(len(passes))
     sgn = -1.0 if inverse else 1.0
@@ -124,48 +157,80 @@ def sweep(psi, n, passes, groups, lut, NT, inverse=False):
         T = int(pd["T"])
         idx = tile_index(n, pd)
         tile = psi[idx]
-        gr = range(pd["g_end"] - 1, pd["g_begin"] - 1, -1) if inverse else range(pd["g_begin"], pd["g_end"])
-        for gi in gr:
-            g = groups[gi]
-            kind = int(g["kind"])
-            pair = kind != DIAG
-            P, nt, li = _layout(g, T, NT, pair)
-            code = _codes(g, T, tile.shape[0], nt, pair)[:, :, None] ^ g["jcode"][:P].astype(np.int64)[None, None, :]
-            cs = lut[int(g["lut"]) + code]
-            c, s = cs[..., 0], sgn * cs[..., 1]
-            if not pair:
-                a = tile[:, li]
-                tile[:, li] = (c - 1j * s) * a
-                continue
-            lj = li ^ int(g["xl"])
-            a, b = tile[:, li], tile[:, lj]
-            if kind == REAL:
-                tile[:, li], tile[:, lj] = c * a - s * b, s * a + c * b
-            else:
-                tile[:, li], tile[:, lj] = c * a - 1j * s * b, c * b - 1j * s * a
+        ntiles = tile.shape[0]
+        g0 = int(pd["g_begin"])
+        bb_, be_ = int(pd["b_begin"]), int(pd["b_end"])
+        brange = range(be_ - 1, bb_ - 1, -1) if inverse else range(bb_, be_)
+        for bi in brange:
+            b = blocks[bi]
+            d, J, nthr, l, lane, warp = _block_layout(b, T, NT)
+            amps = tile[:, l]                      # [t, tid, j, c]
+            gb_, ge_ = int(b["g_begin"]), int(b["g_end"])
+            grange = range(ge_ - 1, gb_ - 1, -1) if inverse else range(gb_, ge_)
+            for gk in grange:
+                g = groups[g0 + gk]
+                code = _block_codes(g, d, J, lane, warp, _tilecode(g, T, ntiles))
+                cs = lut[int(g["lut"]) + code]
+                c, s = cs[..., 0], sgn * cs[..., 1]
+                kind = int(g["kind"])
+                if kind == DIAG:
+                    amps = (c - 1j * s) * amps
+                    continue
+                ci, cj = _pair_combos(int(g["a"]), d)
+                x, y = amps[..., ci], amps[..., cj]
+                cc, ss = c[..., ci], s[..., ci]
+                if kind == REAL:
+                    amps[..., ci], amps[..., cj] = cc * x - ss * y, ss * x + cc * y
+                else:
+                    amps[..., ci], amps[..., cj] = cc * x - 1j * ss * y, cc * y - 1j * ss * x
+            tile[:, l] = amps
         psi[idx] = tile
     return psi
 
 
-def expectation(psi, n, passes, groups, lut, NT):
+def expectation(psi, n, passes, groups, blocks, lut, NT):
     """(sum_t c_t <P_t>, <psi|psi>) walking the Hamiltonian schedule."""
     e = 0.0
     for pd in passes:
         T = int(pd["T"])
         idx = tile_index(n, pd)
         tile = psi[idx]
-        for gi in range(pd["g_begin"], pd["g_end"]):
-            g = groups[gi]
-            pair = int(g["kind"]) != DIAG
-            P, nt, li = _layout(g, T, NT, pair)
-            code = _codes(g, T, tile.shape[0], nt, pair)[:, :, None] ^ g["jcode"][:P].astype(np.int64)[None, None, :]
-            rq = lut[int(g["lut"]) + code]
-            if not pair:
-                e += float(np.sum(rq[..., 0] * np.abs(tile[:, li]) ** 2))
-            else:
-                w = np.conj(tile[:, li]) * tile[:, li ^ int(g["xl"])]
-                e += float(np.sum(2 * (rq[..., 0] * w.real + rq[..., 1] * w.imag)))
+        ntiles = tile.shape[0]
+        g0 = int(pd["g_begin"])
+        for bi in range(pd["b_begin"], pd["b_end"]):
+            b = blocks[bi]
+            d, J, nthr, l, lane, warp = _block_layout(b, T, NT)
+            amps = tile[:, l]
+            for gk in range(int(b["g_begin"]), int(b["g_end"])):
+                g = groups[g0 + gk]
+                code = _block_codes(g, d, J, lane, warp, _tilecode(g, T, ntiles))
+                rq = lut[int(g["lut"]) + code]
+                if int(g["kind"]) == DIAG:
+                    e += float(np.sum(rq[..., 0] * np.abs(amps) ** 2))
+                    continue
+                ci, cj = _pair_combos(int(g["a"]), d)
+                w = np.conj(amps[..., ci]) * amps[..., cj]
+                e += float(np.sum(2 * (rq[..., ci, 0] * w.real + rq[..., ci, 1] * w.imag)))
     return e, float(np.vdot(psi, psi).real)
+
+
+def _pair_layout(g, T, NT):
+    pair = int(g["kind"]) != DIAG
+    per = 1 << (T - 1) if pair else 1 << T
+    P = max(1, per // NT)
+    nthr = min(NT, per)
+    tid = np.arange(nthr, dtype=np.uint64)
+    if pair:
+        li = _insert0(tid, int(g["pivot"]))[:, None] | g["pu"][:P].astype(np.uint64)[None, :]
+    else:
+        li = tid[:, None] + np.uint64(NT) * np.arange(P, dtype=np.uint64)[None, :]
+    lane, warp = (tid % 32).astype(np.int64), (tid // 32).astype(np.int64)
+    return P, li.astype(np.int64), lane, warp
+
+
+def _pair_codes(g, P, lane, warp, tcode):
+    th = g["plane"][lane].astype(np.int64) ^ g["pwarp"][warp].astype(np.int64)
+    return tcode[:, None, None] ^ th[None, :, None] ^ g["pjcode"][:P].astype(np.int64)[None, None, :]
 
 
 def happly(psi, n, passes, groups, lut, NT):
@@ -177,11 +242,10 @@ def happly(psi, n, passes, groups, lut, NT):
         tl = lam[idx]
         for gi in range(pd["g_begin"], pd["g_end"]):
             g = groups[gi]
-            pair = int(g["kind"]) != DIAG
-            P, nt, li = _layout(g, T, NT, pair)
-            code = _codes(g, T, tp.shape[0], nt, pair)[:, :, None] ^ g["jcode"][:P].astype(np.int64)[None, None, :]
+            P, li, lane, warp = _pair_layout(g, T, NT)
+            code = _pair_codes(g, P, lane, warp, _tilecode(g, T, tp.shape[0]))
             rq = lut[int(g["lut"]) + code]
-            if not pair:
+            if int(g["kind"]) == DIAG:
                 tl[:, li] += rq[..., 0] * tp[:, li]
             else:
                 lj = li ^ int(g["xl"])
@@ -204,13 +268,12 @@ def reverse(psi, lam, n, passes, groups, lut, signmask, NT):
         for gi in range(pd["g_end"] - 1, pd["g_begin"] - 1, -1):
             g = groups[gi]
             kind = int(g["kind"])
-            pair = kind != DIAG
-            P, nt, li = _layout(g, T, NT, pair)
-            code = _codes(g, T, tp.shape[0], nt, pair)[:, :, None] ^ g["jcode"][:P].astype(np.int64)[None, None, :]
+            P, li, lane, warp = _pair_layout(g, T, NT)
+            code = _pair_codes(g, P, lane, warp, _tilecode(g, T, tp.shape[0]))
             cs = lut[int(g["lut"]) + code]
             c, s = cs[..., 0], -cs[..., 1]
             k0 = int(pd["rot_begin"]) + int(g["rot0"])
-            if not pair:
+            if kind == DIAG:
                 a, b = tp[:, li], tl[:, li]
                 val = (np.conj(b) * a).imag
             else:
@@ -221,9 +284,10 @@ def reverse(psi, lam, n, passes, groups, lut, signmask, NT):
                 else:
                     val = (np.conj(la) * pb + np.conj(lb) * pa).imag
             for k in range(int(g["m"])):
-                sign = 1.0 - 2.0 * ((signmask[k0 + k].astype(np.uint64) >> code.astype(np.uint64)) & np.uint64(1)).astype(np.float64)
+                sign = 1.0 - 2.0 * ((signmask[k0 + k].astype(np.uint64) >> code.astype(np.uint64))
+                                    & np.uint64(1)).astype(np.float64)
                 g_out[k0 + k] += float(np.sum(sign * val))
-            if not pair:
+            if kind == DIAG:
                 tp[:, li] = (c - 1j * s) * a
                 tl[:, li] = (c - 1j * s) * b
             elif kind == REAL:

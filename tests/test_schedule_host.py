@@ -110,7 +110,7 @@ def _random_rotations(rng, n, k, p_zero=0.1):
 def test_tiles_partition_the_state(lib, n, T, C):
     rng = np.random.default_rng(n)
     x, z, phi = _random_rotations(rng, n, 60)
-    passes, groups, lut, sm = emu.rot_plan(lib, n, x, z, phi, T, C)
+    passes, groups, blocks, lut, sm = emu.rot_plan(lib, n, x, z, phi, T, C)
     for pd in passes:
         idx = emu.tile_index(n, pd)
         assert np.array_equal(np.sort(idx.ravel()), np.arange(1 << n, dtype=np.uint64))
@@ -123,13 +123,13 @@ def test_tiles_partition_the_state(lib, n, T, C):
 def test_schedule_sweep_matches_oracle(lib, n, T, C, seed):
     rng = np.random.default_rng(100 + seed)
     x, z, phi = _random_rotations(rng, n, 120)
-    passes, groups, lut, sm = emu.rot_plan(lib, n, x, z, phi, T, C)
+    passes, groups, blocks, lut, sm = emu.rot_plan(lib, n, x, z, phi, T, C)
     psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
     psi0 /= np.linalg.norm(psi0)
     ref = sv.apply_rotations(psi0, x, z, phi)
-    got = emu.sweep(psi0, n, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    got = emu.sweep(psi0, n, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta())
     assert np.max(np.abs(got - ref)) < 1e-12
-    back = emu.sweep(got, n, passes, groups, lut, lib.q2_debug_threads_per_cta(), inverse=True)
+    back = emu.sweep(got, n, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta(), inverse=True)
     assert np.max(np.abs(back - psi0)) < 1e-12
 
 
@@ -138,9 +138,9 @@ def test_schedule_uccsd_matches_oracle(lib, n, ne, T, C):
     w = uccsd_energy(n, ne, seed=1)
     a = w.ansatz
     phi = a.angles(np.random.default_rng(3).normal(0, 0.3, size=a.n_params))
-    passes, groups, lut, sm = emu.rot_plan(lib, n, a.x, a.z, phi, T, C)
+    passes, groups, blocks, lut, sm = emu.rot_plan(lib, n, a.x, a.z, phi, T, C)
     ref = sv.apply_rotations(sv.hf_state(n, ne), a.x, a.z, phi)
-    got = emu.sweep(sv.hf_state(n, ne), n, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    got = emu.sweep(sv.hf_state(n, ne), n, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta())
     assert np.max(np.abs(got - ref)) < 1e-12
 
 
@@ -153,9 +153,9 @@ def test_schedule_expectation_and_happly(lib, n, T, C, seed):
     z = rng.integers(0, 1 << n, size=k).astype(np.uint64)
     c = rng.normal(size=k)
     x[k // 2:k // 2 + 10] = x[k // 2]            # a group with many terms
-    passes, groups, lut = emu.ham_plan(lib, n, x, z, c, T, C)
+    passes, groups, blocks, lut = emu.ham_plan(lib, n, x, z, c, T, C)
     psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
-    e, nrm = emu.expectation(psi, n, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    e, nrm = emu.expectation(psi, n, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta())
     assert abs(e - sv.expectation(psi, x, z, c)) < 1e-9 * max(1.0, abs(e))
     lam = emu.happly(psi, n, passes, groups, lut, lib.q2_debug_threads_per_cta())
     assert np.max(np.abs(lam - sv.apply_hamiltonian(psi, x, z, c))) < 1e-11
@@ -163,9 +163,9 @@ def test_schedule_expectation_and_happly(lib, n, T, C, seed):
 
 def test_schedule_chemistry_hamiltonian(lib):
     w = uccsd_energy(10, 5, seed=2)
-    passes, groups, lut = emu.ham_plan(lib, 10, w.ham.x, w.ham.z, w.ham.c, 8, 4)
+    passes, groups, blocks, lut = emu.ham_plan(lib, 10, w.ham.x, w.ham.z, w.ham.c, 8, 4)
     psi = sv.apply_rotations(sv.hf_state(10, 5), w.ansatz.x, w.ansatz.z, w.angles())
-    e, nrm = emu.expectation(psi, 10, passes, groups, lut, lib.q2_debug_threads_per_cta())
+    e, nrm = emu.expectation(psi, 10, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta())
     assert abs(e - sv.expectation(psi, w.ham.x, w.ham.z, w.ham.c)) < 1e-11
 
 
@@ -182,9 +182,9 @@ def test_schedule_reverse_gradient(lib, n, ne, T, C):
     PH = np.concatenate([phi, p2])
     e_ref, g_ref = sv.energy_and_gradient(n, ne, X, Z, PH, w.ham.x, w.ham.z, w.ham.c)
     NT = lib.q2_debug_threads_per_cta()
-    passes, groups, lut, sm = emu.rot_plan(lib, n, X, Z, PH, T, C)
-    hp, hg, hl = emu.ham_plan(lib, n, w.ham.x, w.ham.z, w.ham.c, T, C)
-    psi = emu.sweep(sv.hf_state(n, ne), n, passes, groups, lut, NT)
+    passes, groups, blocks, lut, sm = emu.rot_plan(lib, n, X, Z, PH, T, C)
+    hp, hg, hb, hl = emu.ham_plan(lib, n, w.ham.x, w.ham.z, w.ham.c, T, C)
+    psi = emu.sweep(sv.hf_state(n, ne), n, passes, groups, blocks, lut, NT)
     lam = emu.happly(psi, n, hp, hg, hl, NT)
     assert abs(np.vdot(psi, lam).real - e_ref) < 1e-11
     psi_b, lam_b, g = emu.reverse(psi, lam, n, passes, groups, lut, sm, NT)
@@ -199,7 +199,7 @@ def test_schedule_fusion_depth_32_qubits(lib):
     pool = excitations(32, 16)
     chosen = [pool[k] for k in rng.permutation(len(pool))[:200]]
     a = uccsd_rotations(32, 16, exc_list=chosen)
-    passes, groups, lut, sm = emu.rot_plan(lib, 32, a.x, a.z, np.zeros(a.n_rot), 12, 4)
+    passes, groups, blocks, lut, sm = emu.rot_plan(lib, 32, a.x, a.z, np.zeros(a.n_rot), 12, 4)
     rots_per_pass = a.n_rot / len(passes)
     assert len(groups) == 200
     assert rots_per_pass > 40          # one tile dimension per excitation
