@@ -112,6 +112,34 @@ q2_status q2_expectation(const void *psi_dev, int n, q2_dtype dtype, const q2_ha
                          double *energy_out, double *norm_out, void *stream);
 
 /*
+ * The energy of q2_expectation, computed without allocating device memory.
+ * The paper has no counterpart: this is a calling convention of this library.
+ *
+ * For callers that may not allocate device memory while they run: code whose
+ * device memory belongs to a framework's own pool, which forbids direct
+ * driver allocations, or a latency-critical loop in which an allocation, and
+ * the device-wide synchronization a free can imply, is not acceptable.
+ * Where q2_expectation takes temporary device memory, this call uses one
+ * fixed library buffer of Q2_NOALLOC_SCRATCH_BYTES (4 MiB): a static device
+ * array that every GPU which loads the library holds until the process
+ * exits.  It receives the per-CTA partial sums, the two result slots and a
+ * copy of the Hamiltonian's group, block and LUT tables (uploaded on every
+ * call, so the handle's own device tables are not needed).
+ * Arguments and results are those of q2_expectation.  Extra error:
+ * Q2_ERR_INVALID if the tables and partial sums do not fit the buffer (the
+ * message gives the bytes needed); nothing is launched then.  The first call
+ * on a device looks up the buffer's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream
+ * capture.  Every call shares the buffer, which keeps the last call's
+ * contents (nothing in it needs to start at zero): calls that can overlap on
+ * the GPU (other streams, other host threads on the same device) race, and
+ * the caller must serialize them.  Synchronizes `stream`.
+ */
+#define Q2_NOALLOC_SCRATCH_BYTES (4u << 20)
+q2_status q2_expectation_noalloc(const void *psi_dev, int n, q2_dtype dtype, const q2_ham *ham,
+                                 double *energy_out, double *norm_out, void *stream);
+
+/*
  * lambda = H psi (the first step of Algorithm 1's backward pass).  psi_dev,
  * lam_dev: device, 2^n amplitudes each, distinct buffers; lam is overwritten.
  * Asynchronous on `stream`.

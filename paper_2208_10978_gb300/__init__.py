@@ -60,6 +60,7 @@ _SIGS = {
     "q2_batch_workspace_bytes": ([_I, _P, _P, _I], _SZ),
     "q2_batch_energy_grad": ([_I, _P, _P, _P, _P, _I, _P, _P, _P, _SZ, _P], _I),
     "q2_set_tile_qubits": ([_I, _I], _I),
+    "q2_expectation_noalloc": ([_P, _I, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P], _I),
 }
 
 

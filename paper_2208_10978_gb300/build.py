@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libq2.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels.cu", "api.cu", "small.cu"]
+CU_SOURCES = ["kernels.cu", "api.cu", "small.cu", "noalloc.cu"]
 CPP_SOURCES = ["schedule.cpp", "serve_core.cpp"]
 HEADERS = ["q2_internal.h", "kernels.h", "small.h"]
 PUBLIC_HEADERS = ["q2.h", "q2_debug.h"]

@@ -736,3 +736,32 @@ q2_status q2_debug_last_timing(double *out8) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ helpers for noalloc.cu
+
+namespace q2 {
+
+// Host schedule of a Hamiltonian for a dtype, built and cached in the handle
+// without any device work; *chunk receives the dtype's low contiguous qubits.
+q2_status ham_host_plan(const q2_ham *hc, q2_dtype d, const HamPlan **plan, int *chunk) {
+  q2_ham *h = const_cast<q2_ham *>(hc);
+  std::lock_guard<std::mutex> g(h->mu);
+  if (!h->planned[d]) {
+    try {
+      h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
+                                  tile_bits(d), g_chunk[d]);
+    } catch (const std::exception &e) {
+      return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
+    }
+    h->planned[d] = true;
+  }
+  *plan = &h->plan[d];
+  *chunk = g_chunk[d];
+  return Q2_OK;
+}
+
+int ham_qubits(const q2_ham *h) { return h->n; }
+
+q2_status set_error(q2_status s, const char *msg) { return fail(s, msg); }
+
+}  // namespace q2
