@@ -244,130 +244,88 @@ template <int TT, int D> struct BlockShape {
   static constexpr int N = 1 << D;
 };
 
-__host__ __device__ constexpr int ctz_const(int c) { return (c & 1) ? 0 : 1 + ctz_const(c >> 1); }
-
-// Per-thread view of a block: basis offsets and the thread's coset base.
-template <int D> struct BlockRegs {
-  uint32_t vb[D];
-  uint32_t bt;
-  __device__ __forceinline__ void init(const BlockDesc &B, uint32_t tid) {
-    bt = tid;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      vb[i] = B.comb[1 << i];
-      bt = insert_zero(bt, B.piv[i]);
-    }
-  }
-  // local index of combo c of the coset with offset bj (XOR chain, compile-time c)
-  template <int N>
-  __device__ __forceinline__ void addresses(uint32_t bj, uint32_t (&a)[N]) const {
-    a[0] = bj;
-#pragma unroll
-    for (int c = 1; c < N; ++c) a[c] = a[c & (c - 1)] ^ vb[ctz_const(c)];
-  }
-};
-
-// LUT index of every combo of a group (linear in c: XOR chain of the basis codes).
-template <int D>
-__device__ __forceinline__ void combo_codes(const GroupDesc &g, uint32_t cb, uint32_t (&idx)[1 << D]) {
-  uint32_t beta[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) beta[i] = g.bccode[1 << i];
-  idx[0] = cb ^ g.bccode[0];
-#pragma unroll
-  for (int c = 1; c < (1 << D); ++c) idx[c] = idx[c & (c - 1)] ^ beta[ctz_const(c)];
-}
-
-template <typename R, int D, int A, bool REAL, bool INV>
-__device__ __forceinline__ void coset_rotate(typename Vec2<R>::type (&v)[1 << D], const uint32_t (&idx)[1 << D],
-                                             const typename Vec2<R>::type *L) {
+// Rotate the pairs (c, c ^ A) of a coset held in registers.
+template <typename R, int D, int A>
+__device__ __forceinline__ void coset_pairs(typename Vec2<R>::type (&v)[1 << D], const GroupDesc &g,
+                                            const typename Vec2<R>::type *L, uint32_t cb, R sgn,
+                                            bool real) {
   constexpr int HB = 31 - __builtin_clz(A);
 #pragma unroll
   for (int c = 0; c < (1 << D); ++c) {
     if ((c >> HB) & 1) continue;
-    const auto cs = L[idx[c]];
-    const R sn = INV ? -cs.y : cs.y;
-    if (REAL) rot_real(v[c], v[c ^ A], cs.x, sn);
-    else rot_xrot(v[c], v[c ^ A], cs.x, sn);
+    const auto cs = L[cb ^ g.bccode[c]];
+    if (real) rot_real(v[c], v[c ^ A], cs.x, sgn * cs.y);
+    else rot_xrot(v[c], v[c ^ A], cs.x, sgn * cs.y);
   }
 }
 
-#define Q2_CASE_ROT(AV)                                      \
-  case AV:                                                   \
-    if constexpr (AV < (1 << D)) coset_rotate<R, D, AV, REAL, INV>(v, idx, L); \
-    break;
-
-template <typename R, int D, bool REAL, bool INV>
-__device__ __forceinline__ void coset_rotate_any(int a, typename Vec2<R>::type (&v)[1 << D],
-                                                 const uint32_t (&idx)[1 << D],
-                                                 const typename Vec2<R>::type *L) {
-  switch (a) {
-    Q2_CASE_ROT(1) Q2_CASE_ROT(2) Q2_CASE_ROT(3) Q2_CASE_ROT(4) Q2_CASE_ROT(5) Q2_CASE_ROT(6)
-    Q2_CASE_ROT(7) Q2_CASE_ROT(8) Q2_CASE_ROT(9) Q2_CASE_ROT(10) Q2_CASE_ROT(11) Q2_CASE_ROT(12)
-    Q2_CASE_ROT(13) Q2_CASE_ROT(14) Q2_CASE_ROT(15)
-    default: break;
+template <typename R, int D, int A>
+__device__ __forceinline__ void coset_pairs_any(int a, typename Vec2<R>::type (&v)[1 << D],
+                                                const GroupDesc &g, const typename Vec2<R>::type *L,
+                                                uint32_t cb, R sgn, bool real) {
+  if constexpr (A < (1 << D)) {
+    if (a == A) {
+      coset_pairs<R, D, A>(v, g, L, cb, sgn, real);
+      return;
+    }
+    coset_pairs_any<R, D, A + 1>(a, v, g, L, cb, sgn, real);
   }
 }
 
 // One register block of the sweep.  J cosets per thread (GUARD: at most one).
-template <typename R, int D, int J, bool GUARD, bool INV>
+template <typename R, int D, int J, bool GUARD>
 __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const BlockDesc &B,
-                                            const Stage<R> &s) {
+                                            const Stage<R> &s, R sgn, bool inverse) {
   using C2 = typename Vec2<R>::type;
   constexpr int N = 1 << D;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (GUARD && tid >= (s.amps >> D)) return;
-  BlockRegs<D> br;
-  br.init(B, tid);
+  uint32_t bt = tid;
+#pragma unroll
+  for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
   const int gb = B.g_begin, ge = B.g_end;
 #pragma unroll 1
   for (int j = 0; j < J; ++j) {
-    uint32_t ad[N];
-    br.addresses(br.bt ^ B.uj[j], ad);
+    const uint32_t bj = bt ^ B.uj[j];
     C2 v[N];
 #pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = tile[ad[c]];
+    for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
     for (int k = 0; k < ge - gb; ++k) {
-      const int gi = INV ? ge - 1 - k : gb + k;
+      const int gi = inverse ? ge - 1 - k : gb + k;
       const GroupDesc &g = s.gs[gi];
       const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
       const C2 *L = s.lut + g.lut;
-      uint32_t idx[N];
-      combo_codes<D>(g, cb, idx);
-      const int kind = g.kind;
-      if (kind == KIND_DIAG) {
+      if (g.kind == KIND_DIAG) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-          const C2 cs = L[idx[c]];
-          phase(v[c], cs.x, INV ? -cs.y : cs.y);
+          const C2 cs = L[cb ^ g.bccode[c]];
+          phase(v[c], cs.x, sgn * cs.y);
         }
-      } else if (kind == KIND_REAL) {
-        coset_rotate_any<R, D, true, INV>(g.a, v, idx, L);
       } else {
-        coset_rotate_any<R, D, false, INV>(g.a, v, idx, L);
+        coset_pairs_any<R, D, 1>(g.a, v, g, L, cb, sgn, g.kind == KIND_REAL);
       }
     }
 #pragma unroll
-    for (int c = 0; c < N; ++c) tile[ad[c]] = v[c];
+    for (int c = 0; c < N; ++c) tile[bj ^ B.comb[c]] = v[c];
   }
 }
 
-template <typename R, int TT, bool GUARD, bool INV>
+template <typename R, int TT, bool GUARD>
 __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, const BlockDesc &B,
-                                                const Stage<R> &s) {
+                                                const Stage<R> &s, R sgn, bool inverse) {
   if constexpr (GUARD) {
-    sweep_block<R, 1, 1, true, INV>(tile, B, s);
+    sweep_block<R, 1, 1, true>(tile, B, s, sgn, inverse);
   } else {
     switch (B.d) {
-      case 1: sweep_block<R, 1, BlockShape<TT, 1>::J, false, INV>(tile, B, s); break;
+      case 1: sweep_block<R, 1, BlockShape<TT, 1>::J, false>(tile, B, s, sgn, inverse); break;
       case 2:
-        if constexpr (TT >= 10) sweep_block<R, 2, BlockShape<TT, 2>::J, false, INV>(tile, B, s);
+        if constexpr (TT >= 10) sweep_block<R, 2, BlockShape<TT, 2>::J, false>(tile, B, s, sgn, inverse);
         break;
       case 3:
-        if constexpr (TT >= 11) sweep_block<R, 3, BlockShape<TT, 3>::J, false, INV>(tile, B, s);
+        if constexpr (TT >= 11) sweep_block<R, 3, BlockShape<TT, 3>::J, false>(tile, B, s, sgn, inverse);
         break;
       case 4:
-        if constexpr (TT >= 12) sweep_block<R, 4, BlockShape<TT, 4>::J, false, INV>(tile, B, s);
+        if constexpr (TT >= 12) sweep_block<R, 4, BlockShape<TT, 4>::J, false>(tile, B, s, sgn, inverse);
         break;
     }
   }
@@ -375,9 +333,10 @@ __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, co
 
 // ------------------------------------------------------------------ rotation sweep
 
-template <typename R, bool STREAM, int TT, bool GUARD, bool INV>
-__device__ __forceinline__ void sweep_pass(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                                           const BlockDesc *blocks, const typename Vec2<R>::type *lut) {
+template <typename R, bool STREAM, int TT, bool GUARD>
+__global__ void __launch_bounds__(NT, 3) k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups,
+                                                 const BlockDesc *blocks,
+                                                 const typename Vec2<R>::type *lut, int inverse) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -386,6 +345,7 @@ __device__ __forceinline__ void sweep_pass(R *psi, int n, const PassDesc &pd, co
   C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
+  const R sgn = inverse ? (R)-1 : (R)1;
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
@@ -393,21 +353,13 @@ __device__ __forceinline__ void sweep_pass(R *psi, int n, const PassDesc &pd, co
     tile_codes(st, ng, t);
     __syncthreads();
     for (int k = 0; k < nb; ++k) {
-      const int b = INV ? nb - 1 - k : k;
-      sweep_block_any<R, TT, GUARD, INV>(tile, st.bs[b], st);
+      const int b = inverse ? nb - 1 - k : k;
+      sweep_block_any<R, TT, GUARD>(tile, st.bs[b], st, sgn, inverse != 0);
       __syncthreads();
     }
     store_tile<R, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
     __syncthreads();
   }
-}
-
-template <typename R, bool STREAM, int TT, bool GUARD>
-__global__ void __launch_bounds__(NT, 3) k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups,
-                                                 const BlockDesc *blocks,
-                                                 const typename Vec2<R>::type *lut, int inverse) {
-  if (inverse) sweep_pass<R, STREAM, TT, GUARD, true>(psi, n, pd, groups, blocks, lut);
-  else sweep_pass<R, STREAM, TT, GUARD, false>(psi, n, pd, groups, blocks, lut);
 }
 
 // ------------------------------------------------------------------ reductions
@@ -440,14 +392,14 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 // ------------------------------------------------------------------ expectation
 
 template <typename R, int D, int A>
-__device__ __forceinline__ R coset_expect(const typename Vec2<R>::type (&v)[1 << D], const uint32_t (&idx)[1 << D],
-                                          const typename Vec2<R>::type *L) {
+__device__ __forceinline__ R coset_expect(const typename Vec2<R>::type (&v)[1 << D], const GroupDesc &g,
+                                          const typename Vec2<R>::type *L, uint32_t cb) {
   constexpr int HB = 31 - __builtin_clz(A);
   R s = 0;
 #pragma unroll
   for (int c = 0; c < (1 << D); ++c) {
     if ((c >> HB) & 1) continue;
-    const auto rq = L[idx[c]];
+    const auto rq = L[cb ^ g.bccode[c]];
     const auto a = v[c], b = v[c ^ A];
     // w = conj(a) b ; contribution 2 (R Re w + Q Im w), factor 2 applied by the caller
     s += rq.x * (a.x * b.x + a.y * b.y) + rq.y * (a.x * b.y - a.y * b.x);
@@ -455,21 +407,16 @@ __device__ __forceinline__ R coset_expect(const typename Vec2<R>::type (&v)[1 <<
   return s;
 }
 
-#define Q2_CASE_EXP(AV)                                                         \
-  case AV:                                                                      \
-    if constexpr (AV < (1 << D)) return coset_expect<R, D, AV>(v, idx, L);      \
-    break;
-
-template <typename R, int D>
+template <typename R, int D, int A>
 __device__ __forceinline__ R coset_expect_any(int a, const typename Vec2<R>::type (&v)[1 << D],
-                                              const uint32_t (&idx)[1 << D], const typename Vec2<R>::type *L) {
-  switch (a) {
-    Q2_CASE_EXP(1) Q2_CASE_EXP(2) Q2_CASE_EXP(3) Q2_CASE_EXP(4) Q2_CASE_EXP(5) Q2_CASE_EXP(6)
-    Q2_CASE_EXP(7) Q2_CASE_EXP(8) Q2_CASE_EXP(9) Q2_CASE_EXP(10) Q2_CASE_EXP(11) Q2_CASE_EXP(12)
-    Q2_CASE_EXP(13) Q2_CASE_EXP(14) Q2_CASE_EXP(15)
-    default: break;
+                                              const GroupDesc &g, const typename Vec2<R>::type *L,
+                                              uint32_t cb) {
+  if constexpr (A < (1 << D)) {
+    if (a == A) return coset_expect<R, D, A>(v, g, L, cb);
+    return coset_expect_any<R, D, A + 1>(a, v, g, L, cb);
+  } else {
+    return (R)0;
   }
-  return (R)0;
 }
 
 template <typename R, int D, int J, bool GUARD>
@@ -479,31 +426,29 @@ __device__ __forceinline__ void expect_block(const typename Vec2<R>::type *tile,
   constexpr int N = 1 << D;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (GUARD && tid >= (s.amps >> D)) return;
-  BlockRegs<D> br;
-  br.init(B, tid);
+  uint32_t bt = tid;
+#pragma unroll
+  for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
   const int gb = B.g_begin, ge = B.g_end;
 #pragma unroll 1
   for (int j = 0; j < J; ++j) {
-    uint32_t ad[N];
-    br.addresses(br.bt ^ B.uj[j], ad);
+    const uint32_t bj = bt ^ B.uj[j];
     C2 v[N];
 #pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = tile[ad[c]];
-    R e = 0;
+    for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
     for (int gi = gb; gi < ge; ++gi) {
       const GroupDesc &g = s.gs[gi];
       const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
       const C2 *L = s.lut + g.lut;
-      uint32_t idx[N];
-      combo_codes<D>(g, cb, idx);
+      R e = 0;
       if (g.kind == KIND_DIAG) {
 #pragma unroll
-        for (int c = 0; c < N; ++c) e += L[idx[c]].x * (v[c].x * v[c].x + v[c].y * v[c].y);
+        for (int c = 0; c < N; ++c) e += L[cb ^ g.bccode[c]].x * (v[c].x * v[c].x + v[c].y * v[c].y);
       } else {
-        e += 2 * coset_expect_any<R, D>(g.a, v, idx, L);
+        e = 2 * coset_expect_any<R, D, 1>(g.a, v, g, L, cb);
       }
+      acc.add(e);
     }
-    acc.add(e);
   }
 }
 
@@ -521,6 +466,7 @@ __device__ __forceinline__ void expect_block_any(const typename Vec2<R>::type *t
       case 3:
         if constexpr (TT >= 11) expect_block<R, 3, BlockShape<TT, 3>::J, false>(tile, B, s, acc);
         break;
+
     }
   }
 }
