@@ -260,11 +260,23 @@ class Ansatz:
 
 
 def alloc_workspace(nbytes, device="cuda"):
-    """Device byte buffer (torch) with a 256-byte aligned start."""
+    """Device byte buffer (torch uint8) with a 256-byte aligned start.
+
+    Backed by 8-byte elements so that slices of it can be viewed as state
+    vectors (see workspace_state)."""
     torch = _torch()
-    buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
-    off = (-buf.data_ptr()) % 256
-    return buf[off:off + int(nbytes)]
+    n8 = (int(nbytes) + 7) // 8
+    buf = torch.empty(n8 + 32, dtype=torch.float64, device=device)
+    off = ((-buf.data_ptr()) % 256) // 8
+    return buf[off:off + n8].view(torch.uint8)[:int(nbytes)]
+
+
+def workspace_state(workspace, n, dtype="complex64"):
+    """The 2^n-amplitude state held at the start of a q2_vqe_energy_grad workspace."""
+    torch = _torch()
+    td = _torch_dtype(_dtype_code(dtype))
+    nbytes = (1 << n) * (8 if td == torch.complex64 else 16)
+    return workspace[:nbytes].view(td)
 
 
 def vqe_energy_grad(ansatz, ham, theta, dtype="complex64", want_grad=True, workspace=None):
