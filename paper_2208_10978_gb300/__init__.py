@@ -301,6 +301,39 @@ def vqe_energy_grad(ansatz, ham, theta, dtype="complex64", want_grad=True, works
     return e.value, g, workspace
 
 
+def batch_energy_grad(ansatze, hams, thetas, want_grads, dtype="complex64", workspace=None):
+    """Evaluate many small problems (n <= 12) in one persistent launch.
+
+    Returns (energies, grads, workspace); grads[b] is None where want_grads[b]
+    is false.  Each request's result does not depend on the rest of the batch.
+    """
+    nb = len(ansatze)
+    if not (len(hams) == len(thetas) == len(want_grads) == nb):
+        raise ValueError("per-request lists must have equal length")
+    if nb == 0:
+        return np.zeros(0), [], workspace
+    d = _dtype_code(dtype)
+    A = (_P * nb)(*[a.handle for a in ansatze])
+    H = (_P * nb)(*[h.handle for h in hams])
+    th = [_f64(t) for t in thetas]
+    for a, t in zip(ansatze, th):
+        if len(t) != a.n_params:
+            raise ValueError("theta has the wrong length")
+    TH = (_P * nb)(*[t.ctypes.data for t in th])
+    wg = (ctypes.c_int * nb)(*[1 if w else 0 for w in want_grads])
+    grads = [np.zeros(a.n_params) if w else None for a, w in zip(ansatze, want_grads)]
+    G = (_P * nb)(*[g.ctypes.data if g is not None else None for g in grads])
+    need = lib().q2_batch_workspace_bytes(nb, A, H, d)
+    if need == 0:
+        raise Q2Error(Q2_ERR_INVALID, lib().q2_last_error().decode(errors="replace"))
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    e = np.zeros(nb)
+    _check(lib().q2_batch_energy_grad(nb, A, H, TH, wg, d, _np_ptr(e), G, ctypes.c_void_p(workspace.data_ptr()),
+                                      workspace.numel(), _stream_ptr()))
+    return e, grads, workspace
+
+
 def set_tile_qubits(dtype, t):
     _check(lib().q2_set_tile_qubits(_dtype_code(dtype), int(t)))
 
@@ -310,5 +343,5 @@ from .autograd import Energy  # noqa: E402  (needs the names above)
 __all__ = [
     "C64", "C128", "Q2Error", "lib", "library_path", "new_state", "state_init_hf",
     "apply_pauli_rotations", "Hamiltonian", "Ansatz", "alloc_workspace", "vqe_energy_grad",
-    "set_tile_qubits", "Energy",
+    "set_tile_qubits", "Energy", "batch_energy_grad", "workspace_state",
 ]

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "api.cu", "small.cu", "noalloc.cu"]
 CPP_SOURCES = ["schedule.cpp", "serve_core.cpp"]
 HEADERS = ["q2_internal.h", "kernels.h", "small.h"]
-PUBLIC_HEADERS = ["q2.h", "q2_debug.h"]
+PUBLIC_HEADERS = ["q2.h", "q2_debug.h", "q2_serve.h"]
 
 
 def _nvcc():

@@ -14,6 +14,7 @@
 #include "../../include/q2.h"
 #include "kernels.h"
 #include "q2_internal.h"
+#include "small.h"
 
 using namespace q2;
 
@@ -148,6 +149,10 @@ struct q2_ham {
   HamPlan plan[2];
   bool planned[2] = {false, false};
   DevTables dev[2];
+  // single-tile plan (identity local basis) for the batched small-state path
+  HamPlan splan;
+  bool splanned = false;
+  DevTables sdev[2];
   std::mutex mu;
 };
 
@@ -160,6 +165,10 @@ struct q2_ansatz {
   RotPlan plan[2];
   bool planned[2] = {false, false};
   DevTables dev[2];
+  RotPlan splan;
+  bool splanned = false;
+  DevTables sdev;
+  int32_t *sgrot = nullptr;     // device: first rotation of each group of splan
   std::mutex mu;
 };
 
@@ -396,6 +405,119 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
   return Q2_OK;
 }
 
+// ---- batched small-state path: single-tile plans (identity local basis)
+
+struct BatchSlot {
+  size_t lut_off, out_off, stage_end;
+};
+
+const RotPlan &small_rot_plan(const q2_ansatz *ac) {
+  q2_ansatz *a = const_cast<q2_ansatz *>(ac);
+  std::lock_guard<std::mutex> g(a->mu);
+  if (!a->splanned) {
+    a->splan = build_rot_plan(a->n, (int64_t)a->x.size(), a->x.data(), a->z.data(), a->n, a->n);
+    a->splanned = true;
+  }
+  return a->splan;
+}
+
+q2_status small_ansatz_tables(const q2_ansatz *ac, const DevTables **dev, const int32_t **grot) {
+  const RotPlan &p = small_rot_plan(ac);
+  q2_ansatz *a = const_cast<q2_ansatz *>(ac);
+  std::lock_guard<std::mutex> g(a->mu);
+  DevTables &t = a->sdev;
+  int device = 0;
+  Q2_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+  if (t.ready && t.device != device) return fail(Q2_ERR_INVALID, "ansatz handle used on another device");
+  if (!t.ready) {
+    const size_t gb = sizeof(GroupDesc) * std::max<size_t>(1, p.groups.size());
+    const size_t sb = sizeof(uint64_t) * std::max<size_t>(1, p.signmask.size());
+    const size_t rb = sizeof(int32_t) * std::max<size_t>(1, p.grp_rot_begin.size());
+    if (cudaMalloc(&t.groups, gb) != cudaSuccess || cudaMalloc(&t.signmask, sb) != cudaSuccess ||
+        cudaMalloc(&a->sgrot, rb) != cudaSuccess) {
+      t.release();
+      return fail(Q2_ERR_OOM, "cudaMalloc(small rotation tables)");
+    }
+    std::vector<int32_t> gr(p.grp_rot_begin.begin(), p.grp_rot_begin.end());
+    if (!p.groups.empty())
+      Q2_CUDA(cudaMemcpy(t.groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size(), cudaMemcpyHostToDevice),
+              "upload groups");
+    if (!p.signmask.empty())
+      Q2_CUDA(cudaMemcpy(t.signmask, p.signmask.data(), sizeof(uint64_t) * p.signmask.size(),
+                         cudaMemcpyHostToDevice), "upload sign masks");
+    if (!gr.empty())
+      Q2_CUDA(cudaMemcpy(a->sgrot, gr.data(), sizeof(int32_t) * gr.size(), cudaMemcpyHostToDevice),
+              "upload group rotations");
+    t.device = device;
+    t.T = p.T;
+    t.ready = true;
+  }
+  *dev = &t;
+  *grot = a->sgrot;
+  return Q2_OK;
+}
+
+q2_status small_ham_tables(const q2_ham *hc, q2_dtype d, const HamPlan **plan, const DevTables **dev) {
+  q2_ham *h = const_cast<q2_ham *>(hc);
+  std::lock_guard<std::mutex> g(h->mu);
+  if (!h->splanned) {
+    try {
+      h->splan = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(), h->n, h->n);
+    } catch (const std::exception &e) {
+      return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
+    }
+    h->splanned = true;
+  }
+  DevTables &t = h->sdev[d];
+  int device = 0;
+  Q2_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+  if (t.ready && t.device != device) return fail(Q2_ERR_INVALID, "Hamiltonian handle used on another device");
+  if (!t.ready) {
+    const HamPlan &p = h->splan;
+    const size_t gb = sizeof(GroupDesc) * std::max<size_t>(1, p.groups.size());
+    std::vector<unsigned char> lb = lut_bytes(p.lut2, d);
+    if (cudaMalloc(&t.groups, gb) != cudaSuccess || cudaMalloc(&t.lut, std::max<size_t>(16, lb.size())) != cudaSuccess) {
+      t.release();
+      return fail(Q2_ERR_OOM, "cudaMalloc(small Hamiltonian tables)");
+    }
+    if (!p.groups.empty())
+      Q2_CUDA(cudaMemcpy(t.groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size(), cudaMemcpyHostToDevice),
+              "upload groups");
+    if (!lb.empty()) Q2_CUDA(cudaMemcpy(t.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice), "upload LUT");
+    t.device = device;
+    t.T = p.T;
+    t.ready = true;
+  }
+  *plan = &h->splan;
+  *dev = &t;
+  return Q2_OK;
+}
+
+// Workspace of a batch: [items][per-request rotation LUTs][per-request outputs]; the
+// staging image uploaded per call covers items and LUTs.
+q2_status batch_layout(int nreq, const q2_ansatz *const *ansatz, q2_dtype d, std::vector<BatchSlot> *slots,
+                       size_t *total) {
+  const size_t lut_b = d == Q2_C64 ? 2 * sizeof(float) : 2 * sizeof(double);
+  size_t o = align_up(sizeof(BatchItem) * (size_t)std::max(1, nreq), 256);
+  std::vector<BatchSlot> sl(nreq);
+  for (int b = 0; b < nreq; ++b) {
+    if (!ansatz[b]) return fail(Q2_ERR_INVALID, "NULL ansatz");
+    if (ansatz[b]->n > SMALL_MAX_QUBITS) return fail(Q2_ERR_INVALID, "batched requests need n <= 12");
+    const RotPlan &p = small_rot_plan(ansatz[b]);
+    sl[b].lut_off = o;
+    o = align_up(o + lut_b * (size_t)std::max<int64_t>(1, p.lut_entries), 256);
+  }
+  const size_t stage_end = o;
+  for (int b = 0; b < nreq; ++b) {
+    sl[b].out_off = o;
+    sl[b].stage_end = stage_end;
+    o = align_up(o + sizeof(double) * (2 + ansatz[b]->x.size()), 256);
+  }
+  if (slots) *slots = sl;
+  *total = o;
+  return Q2_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -488,6 +610,8 @@ q2_status q2_ham_destroy(q2_ham *ham) {
   if (!ham) return Q2_OK;
   ham->dev[0].release();
   ham->dev[1].release();
+  ham->sdev[0].release();
+  ham->sdev[1].release();
   delete ham;
   return Q2_OK;
 }
@@ -579,6 +703,8 @@ q2_status q2_ansatz_destroy(q2_ansatz *ansatz) {
   if (!ansatz) return Q2_OK;
   ansatz->dev[0].release();
   ansatz->dev[1].release();
+  ansatz->sdev.release();
+  if (ansatz->sgrot) cudaFree(ansatz->sgrot);
   delete ansatz;
   return Q2_OK;
 }
@@ -621,29 +747,101 @@ q2_status q2_vqe_energy_grad(const q2_ansatz *ansatz, const q2_ham *ham, const d
 
 size_t q2_batch_workspace_bytes(int n_requests, const q2_ansatz *const *ansatz, const q2_ham *const *ham,
                                 q2_dtype dtype) {
-  (void)n_requests;
-  (void)ansatz;
-  (void)ham;
-  (void)dtype;
-  return 0;
+  if (n_requests < 0 || (n_requests > 0 && (!ansatz || !ham)) || !valid_dtype(dtype)) return 0;
+  size_t total = 0;
+  if (batch_layout(n_requests, ansatz, dtype, nullptr, &total) != Q2_OK) return 0;
+  return total;
 }
 
 q2_status q2_batch_energy_grad(int n_requests, const q2_ansatz *const *ansatz, const q2_ham *const *ham,
                                const double *const *theta, const int *want_grad, q2_dtype dtype,
                                double *energy_out, double *const *grad_out, void *workspace_dev,
                                size_t workspace_bytes, void *stream) {
-  (void)n_requests;
-  (void)ansatz;
-  (void)ham;
-  (void)theta;
-  (void)want_grad;
-  (void)dtype;
-  (void)energy_out;
-  (void)grad_out;
-  (void)workspace_dev;
-  (void)workspace_bytes;
-  (void)stream;
-  return fail(Q2_ERR_UNSUPPORTED, "batched small-state path not built yet");
+  if (n_requests < 0) return fail(Q2_ERR_INVALID, "negative request count");
+  if (n_requests == 0) return Q2_OK;
+  if (!ansatz || !ham || !theta || !want_grad || !energy_out) return fail(Q2_ERR_INVALID, "NULL argument");
+  if (!valid_dtype(dtype)) return fail(Q2_ERR_INVALID, "unknown dtype");
+  if (!workspace_dev || !aligned(workspace_dev, 256))
+    return fail(Q2_ERR_INVALID, "workspace must be a 256-byte aligned device pointer");
+  for (int b = 0; b < n_requests; ++b) {
+    if (!ansatz[b] || !ham[b] || !theta[b]) return fail(Q2_ERR_INVALID, "NULL request entry");
+    if (ansatz[b]->n > SMALL_MAX_QUBITS) return fail(Q2_ERR_INVALID, "batched requests need n <= 12");
+    if (ham[b]->n != ansatz[b]->n) return fail(Q2_ERR_INVALID, "Hamiltonian and ansatz qubit counts differ");
+    q2_status s = check_finite(ansatz[b]->n_params, theta[b], "theta");
+    if (s != Q2_OK) return s;
+    if (want_grad[b] && (!grad_out || !grad_out[b])) return fail(Q2_ERR_INVALID, "NULL gradient output");
+  }
+  std::vector<BatchSlot> slots;
+  size_t total = 0;
+  q2_status s = batch_layout(n_requests, ansatz, dtype, &slots, &total);
+  if (s != Q2_OK) return s;
+  if (workspace_bytes < total) return fail(Q2_ERR_INVALID, "workspace too small");
+  unsigned char *ws = static_cast<unsigned char *>(workspace_dev);
+  const size_t lut_b = dtype == Q2_C64 ? sizeof(float) : sizeof(double);
+  std::vector<unsigned char> stage(slots.empty() ? 0 : slots.back().stage_end, 0);
+  int max_n = 1, any_grad = 0;
+  for (int b = 0; b < n_requests; ++b) {
+    const q2_ansatz *a = ansatz[b];
+    const DevTables *at;
+    const int32_t *grot;
+    const DevTables *ht;
+    const HamPlan *hp;
+    if ((s = small_ansatz_tables(a, &at, &grot)) != Q2_OK) return s;
+    if ((s = small_ham_tables(ham[b], dtype, &hp, &ht)) != Q2_OK) return s;
+    const RotPlan &rp = a->splan;
+    std::vector<double> phi(a->x.size());
+    for (size_t k = 0; k < phi.size(); ++k) phi[k] = a->coef[k] * theta[b][a->param[k]];
+    std::vector<double> lut2(2 * (size_t)std::max<int64_t>(1, rp.lut_entries));
+    rp.build_lut(phi.data(), lut2.data());
+    unsigned char *dst = stage.data() + slots[b].lut_off;
+    if (dtype == Q2_C64) {
+      float *f = reinterpret_cast<float *>(dst);
+      for (size_t i = 0; i < lut2.size(); ++i) f[i] = (float)lut2[i];
+    } else {
+      std::memcpy(dst, lut2.data(), lut2.size() * sizeof(double));
+    }
+    BatchItem it;
+    std::memset(&it, 0, sizeof(it));
+    it.rg = at->groups;
+    it.grot = grot;
+    it.sm = at->signmask;
+    it.rlut = ws + slots[b].lut_off;
+    it.hg = ht->groups;
+    it.hlut = ht->lut;
+    it.out = reinterpret_cast<double *>(ws + slots[b].out_off);
+    it.nrg = (int32_t)rp.groups.size();
+    it.nhg = (int32_t)hp->groups.size();
+    it.n = a->n;
+    it.n_elec = a->n_elec;
+    it.want_grad = want_grad[b] ? 1 : 0;
+    it.n_rot = (int32_t)a->x.size();
+    std::memcpy(stage.data() + sizeof(BatchItem) * (size_t)b, &it, sizeof(it));
+    max_n = std::max(max_n, a->n);
+    any_grad |= it.want_grad;
+    (void)lut_b;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Q2_CUDA(cudaMemcpyAsync(ws, stage.data(), stage.size(), cudaMemcpyHostToDevice, st), "upload batch");
+  cudaError_t e = dtype == Q2_C64
+                      ? launch_batch<float>(reinterpret_cast<const BatchItem *>(ws), n_requests, max_n, any_grad, st)
+                      : launch_batch<double>(reinterpret_cast<const BatchItem *>(ws), n_requests, max_n, any_grad, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch kernel");
+  const size_t out_begin = slots[0].out_off;
+  const size_t out_bytes = total - out_begin;
+  std::vector<double> outs(out_bytes / sizeof(double));
+  Q2_CUDA(cudaMemcpyAsync(outs.data(), ws + out_begin, out_bytes, cudaMemcpyDeviceToHost, st), "read batch");
+  Q2_CUDA(cudaStreamSynchronize(st), "sync");
+  for (int b = 0; b < n_requests; ++b) {
+    const double *o = outs.data() + (slots[b].out_off - out_begin) / sizeof(double);
+    energy_out[b] = o[0] / o[1];
+    if (want_grad[b]) {
+      const q2_ansatz *a = ansatz[b];
+      double *g = grad_out[b];
+      for (int p = 0; p < a->n_params; ++p) g[p] = 0.0;
+      for (size_t k = 0; k < a->x.size(); ++k) g[a->param[k]] += a->coef[k] * o[2 + k];
+    }
+  }
+  return Q2_OK;
 }
 
 }  // extern "C"
