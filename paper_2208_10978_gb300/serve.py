@@ -99,7 +99,8 @@ class Server:
         import torch
         self._torch = torch
         self.dtype = dtype
-        self.device = torch.device(device)
+        dev = torch.device(device)
+        self.device = dev.index if dev.index is not None else torch.cuda.current_device()
         self.budget = int(budget_bytes)
         self.batch_window_s = batch_window_s
         self.max_batch = max_batch
@@ -195,7 +196,8 @@ class Server:
         with self._lock:
             self._jobs.pop(job.rid, None)
             self._wake.notify_all()
-        job.future.set_result(Result(job.rid, status, energy, grad, path, job.t_submit, t))
+        if not job.future.done():
+            job.future.set_result(Result(job.rid, status, energy, grad, path, job.t_submit, t))
 
     def _admit_loop(self):
         ids = (ctypes.c_int64 * 256)()
@@ -211,7 +213,8 @@ class Server:
                 if not expired and not admitted:
                     self._wake.wait(timeout=0.002)
             for job in expired:
-                job.future.set_result(Result(job.rid, Q2_ERR_TIMEOUT, t_submit=job.t_submit, t_done=self.now()))
+                if not job.future.done():
+                    job.future.set_result(Result(job.rid, Q2_ERR_TIMEOUT, t_submit=job.t_submit, t_done=self.now()))
                 with self._lock:
                     self._jobs.pop(job.rid, None)
             for job in admitted:
@@ -222,7 +225,28 @@ class Server:
                 else:
                     self._large.put(job)
 
+    def _fail_all(self, status):
+        with self._lock:
+            jobs = list(self._jobs.values())
+        for j in jobs:
+            if not j.future.done():
+                j.future.set_result(Result(j.rid, status, t_submit=j.t_submit, t_done=self.now()))
+
     def _batch_loop(self):
+        try:
+            self._batch_loop_body()
+        except Exception:                                  # never leave futures unresolved
+            self._fail_all(Q2_ERR_INVALID)
+            raise
+
+    def _worker_loop(self):
+        try:
+            self._worker_loop_body()
+        except Exception:
+            self._fail_all(Q2_ERR_INVALID)
+            raise
+
+    def _batch_loop_body(self):
         torch = self._torch
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(device=self.device)
@@ -246,8 +270,12 @@ class Server:
             except Q2Error as exc:
                 for j in batch:
                     self._finish(j, exc.status, path="batch")
+            except Exception:
+                for j in batch:
+                    self._finish(j, Q2_ERR_INVALID, path="batch")
+                raise
 
-    def _worker_loop(self):
+    def _worker_loop_body(self):
         torch = self._torch
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(device=self.device)
@@ -263,6 +291,9 @@ class Server:
                 self._finish(job, Q2_OK, e, g, "stream")
             except Q2Error as exc:
                 self._finish(job, exc.status, path="stream")
+            except Exception:
+                self._finish(job, Q2_ERR_INVALID, path="stream")
+                raise
 
 
 def evaluate_alone(problem, theta, want_grad, dtype="complex64", handles=None):
@@ -283,10 +314,11 @@ def problem_from_workload(w, key):
     return Problem(key, w.n, w.n_elec, w.ham.x, w.ham.z, w.ham.c, a.x, a.z, a.param, a.coef, a.n_params)
 
 
-def serve_stream(server, requests, problems, thetas, speed=1.0):
+def serve_stream(server, requests, problems, thetas, speed=1.0, wait_s=900.0):
     """Submit requests at their arrival times (seconds, scaled by 1/speed); wait for all.
 
     Returns (results by rid, wall seconds from the first arrival to the last completion).
+    Raises concurrent.futures.TimeoutError if a result takes longer than wait_s.
     """
     futs = {}
     t_start = time.perf_counter()
@@ -295,6 +327,7 @@ def serve_stream(server, requests, problems, thetas, speed=1.0):
         if delay > 0:
             time.sleep(delay)
         futs[r.rid] = server.submit(r.rid, problems[r.problem_seed], thetas[r.problem_seed], r.want_grad)
-    results = {rid: f.result() for rid, f in futs.items()}
+    deadline = time.perf_counter() + wait_s
+    results = {rid: f.result(timeout=max(0.0, deadline - time.perf_counter())) for rid, f in futs.items()}
     wall = time.perf_counter() - t_start
     return results, wall

@@ -81,7 +81,7 @@ def test_served_stream_same_as_alone(stream_problems):
     budget = 8 * 2**30
     srv = serve.Server(dtype="complex64", budget_bytes=budget, max_slots=16, n_streams=4)
     try:
-        results, wall = serve.serve_stream(srv, reqs, problems, thetas, speed=1.0)
+        results, wall = serve.serve_stream(srv, reqs, problems, thetas, speed=1.0, wait_s=300)
         st = srv.stats()
     finally:
         srv.close()
@@ -115,7 +115,7 @@ def test_starved_queue_times_out(stream_problems):
                        queue_timeout_s=0.001)
     try:
         futs = [srv.submit(1000 + i, big, thetas[big.key], True) for i in range(6)]
-        res = [f.result(timeout=300) for f in futs]
+        res = [f.result(timeout=120) for f in futs]
     finally:
         srv.close()
     status = [r.status for r in res]
