@@ -801,10 +801,36 @@ int blocks_per_sm(K kernel, size_t smem) {
   return b > 0 ? b : 1;
 }
 
+// Largest dynamic shared memory any pass of a kernel instantiation can ask for
+// (tile size T, smallest chunk, fullest staged tables).  The attribute is
+// per-function state shared by every host thread, so it is always set to this
+// fixed value, never to one launch's size.
+size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra) {
+  PassDesc pd{};
+  pd.T = T <= 8 ? 8 : T;
+  pd.C = 1;
+  pd.g_begin = 0;
+  pd.g_end = G_STAGE;
+  pd.b_begin = 0;
+  pd.b_end = G_STAGE;
+  pd.lut_count = LUT_STAGE;
+  SmemLayout L;
+  size_t o = 0;
+  o = align16(o + (size_t)amp_bytes * ((size_t)1 << pd.T) * vectors);
+  o = align16(o + sizeof(uint64_t) * ((size_t)1 << (pd.T - pd.C)));
+  o = align16(o + sizeof(GroupDesc) * G_STAGE);
+  o = align16(o + sizeof(BlockDesc) * G_STAGE);
+  o = align16(o + (size_t)amp_bytes * LUT_STAGE);
+  o = align16(o + sizeof(uint32_t) * G_STAGE);
+  o = align16(o + extra);
+  (void)L;
+  return o;
+}
+
 template <typename K>
-cudaError_t prepare(K kernel, size_t smem) {
-  if (smem > 48 * 1024)
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t prepare(K kernel, size_t smem_cap) {
+  if (smem_cap > 48 * 1024)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
   return cudaSuccess;
 }
 
@@ -877,7 +903,7 @@ cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *gro
   using C2 = typename Vec2<R>::type;
   const size_t smem = smem_layout(sizeof(C2), pd, 1, 0).total;
   auto k = Q2_DISPATCH(k_sweep, R, n, pd.T);
-  cudaError_t e = prepare(k, smem);
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 1, 0));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
   k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), inverse ? 1 : 0);
@@ -889,7 +915,7 @@ int expect_grid(int n, int T, int C) {
   using C2 = typename Vec2<R>::type;
   const size_t smem = tile_smem_bytes(sizeof(C2), T, C, 1);
   auto k = Q2_DISPATCH(k_expect, R, n, T);
-  prepare(k, smem);
+  prepare(k, worst_smem(sizeof(C2), T, 1, sizeof(double) * (NT / 32)));
   return (int)grid_for(1ull << (n - T), blocks_per_sm(k, smem));
 }
 
@@ -900,7 +926,7 @@ cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDe
   using C2 = typename Vec2<R>::type;
   const size_t smem = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32)).total;
   auto k = Q2_DISPATCH(k_expect, R, n, pd.T);
-  cudaError_t e = prepare(k, smem);
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 1, sizeof(double) * (NT / 32)));
   if (e != cudaSuccess) return e;
   k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), partial,
                             first ? 1 : 0);
@@ -920,7 +946,7 @@ cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const
   pq.b_begin = pq.b_end = 0;
   const size_t smem = smem_layout(sizeof(C2), pq, 2, 0).total;
   auto k = Q2_DISPATCH(k_happly, R, n, pd.T);
-  cudaError_t e = prepare(k, smem);
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
   k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), first ? 1 : 0);
@@ -951,7 +977,7 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
   const size_t smem =
       smem_layout(sizeof(C2), pq, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX).total;
   auto k = Q2_DISPATCH(k_reverse, R, n, pd.T);
-  cudaError_t e = prepare(k, smem);
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
   k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), signmask, partial);

@@ -230,8 +230,10 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int max_qubits, in
   if (n_items <= 0) return cudaSuccess;
   const size_t smem = sizeof(C2) * ((size_t)1 << max_qubits) * (any_grad ? 2 : 1);
   auto k = k_batch<R>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // per-function attribute shared by all host threads: always the largest size any batch needs
+  const size_t smem_cap = sizeof(C2) * ((size_t)1 << SMALL_MAX_QUBITS) * 2;
+  if (smem_cap > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
     if (e != cudaSuccess) return e;
   }
   int per_sm = 1, dev = 0, sms = 1;

@@ -59,6 +59,7 @@ class Result:
     path: str = ""
     t_submit: float = 0.0
     t_done: float = 0.0
+    error: str = ""
 
     @property
     def latency(self):
@@ -190,14 +191,14 @@ class Server:
 
     # ------------------------------------------------------------------ loops
 
-    def _finish(self, job, status, energy=float("nan"), grad=None, path=""):
+    def _finish(self, job, status, energy=float("nan"), grad=None, path="", error=""):
         t = self.now()
         self._L.q2_server_complete(self._core, job.rid, t)     # releases its bytes and slot
         with self._lock:
             self._jobs.pop(job.rid, None)
             self._wake.notify_all()
         if not job.future.done():
-            job.future.set_result(Result(job.rid, status, energy, grad, path, job.t_submit, t))
+            job.future.set_result(Result(job.rid, status, energy, grad, path, job.t_submit, t, error))
 
     def _admit_loop(self):
         ids = (ctypes.c_int64 * 256)()
@@ -225,25 +226,25 @@ class Server:
                 else:
                     self._large.put(job)
 
-    def _fail_all(self, status):
+    def _fail_all(self, status, error):
         with self._lock:
             jobs = list(self._jobs.values())
         for j in jobs:
             if not j.future.done():
-                j.future.set_result(Result(j.rid, status, t_submit=j.t_submit, t_done=self.now()))
+                j.future.set_result(Result(j.rid, status, t_submit=j.t_submit, t_done=self.now(), error=error))
 
     def _batch_loop(self):
         try:
             self._batch_loop_body()
-        except Exception:                                  # never leave futures unresolved
-            self._fail_all(Q2_ERR_INVALID)
+        except Exception as exc:                           # never leave futures unresolved
+            self._fail_all(Q2_ERR_INVALID, "batch loop: " + repr(exc))
             raise
 
     def _worker_loop(self):
         try:
             self._worker_loop_body()
-        except Exception:
-            self._fail_all(Q2_ERR_INVALID)
+        except Exception as exc:
+            self._fail_all(Q2_ERR_INVALID, "stream worker: " + repr(exc))
             raise
 
     def _batch_loop_body(self):
@@ -269,10 +270,10 @@ class Server:
                     self._finish(j, Q2_OK, float(ej), gj, "batch")
             except Q2Error as exc:
                 for j in batch:
-                    self._finish(j, exc.status, path="batch")
-            except Exception:
+                    self._finish(j, exc.status, path="batch", error=str(exc))
+            except Exception as exc:
                 for j in batch:
-                    self._finish(j, Q2_ERR_INVALID, path="batch")
+                    self._finish(j, Q2_ERR_INVALID, path="batch", error=repr(exc))
                 raise
 
     def _worker_loop_body(self):
@@ -290,9 +291,9 @@ class Server:
                                                want_grad=job.want_grad, workspace=ws)
                 self._finish(job, Q2_OK, e, g, "stream")
             except Q2Error as exc:
-                self._finish(job, exc.status, path="stream")
-            except Exception:
-                self._finish(job, Q2_ERR_INVALID, path="stream")
+                self._finish(job, exc.status, path="stream", error=str(exc))
+            except Exception as exc:
+                self._finish(job, Q2_ERR_INVALID, path="stream", error=repr(exc))
                 raise
 
 

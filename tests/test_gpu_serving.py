@@ -85,7 +85,8 @@ def test_served_stream_same_as_alone(stream_problems):
         st = srv.stats()
     finally:
         srv.close()
-    assert all(r.status == q2.Q2_OK for r in results.values())
+    bad = [(r.rid, r.status, r.path, r.error) for r in results.values() if r.status != q2.Q2_OK]
+    assert not bad, bad[:4]
     assert st["completed"] == len(reqs) and st["high_water_bytes"] <= budget
     assert st["p99_s"] >= st["p50_s"] > 0
     paths = {r.path for r in results.values()}
