@@ -204,9 +204,10 @@ q2_status q2_batch_energy_grad(int n_requests, const q2_ansatz *const *ansatz,
                                size_t workspace_bytes, void *stream);
 
 /*
- * Tile size tuning: number of qubits held on chip per tile for a dtype
- * (default 12 for Q2_C64, 11 for Q2_C128; allowed 8..13 for Q2_C64 and
- * 8..12 for Q2_C128).  Affects handles
+ * Tile size tuning: number of qubits held on chip per tile of the rotation
+ * passes for a dtype (default 12 for Q2_C64, 11 for Q2_C128; allowed 8..13
+ * for Q2_C64 and 8..12 for Q2_C128).  Hamiltonian passes use one qubit more
+ * (at most 13 for Q2_C64, 12 for Q2_C128).  Affects handles
  * and calls made afterwards.
  */
 q2_status q2_set_tile_qubits(q2_dtype dtype, int tile_qubits);

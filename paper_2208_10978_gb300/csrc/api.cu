@@ -103,6 +103,10 @@ int tile_bits(q2_dtype d) {
   return g_tile[d];
 }
 
+// Hamiltonian passes use one more tile qubit than rotation passes (more groups
+// per pass; measured faster), within the shared-memory limit of H apply's two tiles.
+int ham_tile_bits(q2_dtype d) { return std::min(tile_bits(d) + 1, d == Q2_C64 ? T_LIMIT : T_LIMIT - 1); }
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Device copies of a plan's groups (and optionally a LUT), owned by a handle.
@@ -180,7 +184,7 @@ q2_status ham_tables(const q2_ham *hc, q2_dtype d, const HamPlan **plan, const D
   if (!h->planned[d]) {
     try {
       h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
-                                  tile_bits(d), g_chunk[d]);
+                                  ham_tile_bits(d), g_chunk[d]);
     } catch (const std::exception &e) {
       return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
     }
@@ -947,7 +951,7 @@ q2_status ham_host_plan(const q2_ham *hc, q2_dtype d, const HamPlan **plan, int 
   if (!h->planned[d]) {
     try {
       h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
-                                  tile_bits(d), g_chunk[d]);
+                                  ham_tile_bits(d), g_chunk[d]);
     } catch (const std::exception &e) {
       return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
     }
