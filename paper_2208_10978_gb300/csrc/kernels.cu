@@ -198,38 +198,6 @@ __device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Stage<R
   }
 }
 
-// Asynchronous tile gather (cp.async, 16 bytes per copy, cached in L2 only):
-// the next tile streams into a second shared buffer while the current one is
-// being worked on.
-#ifndef Q2_DOUBLE_BUFFER
-#define Q2_DOUBLE_BUFFER 1
-#endif
-constexpr bool DOUBLE_BUFFER = Q2_DOUBLE_BUFFER != 0;
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <typename R>
-__device__ __forceinline__ void prefetch_tile(const R *src, uint64_t base, const Stage<R> &tc,
-                                              typename Vec16<R>::type *dst) {
-  using V = typename Vec16<R>::type;
-  constexpr int A = Vec16<R>::amps;
-  const uint32_t nv = tc.amps / A;
-  const uint32_t cm = (1u << tc.C) - 1u;
-  const V *g = reinterpret_cast<const V *>(src);
-#pragma unroll 4
-  for (uint32_t v = threadIdx.x; v < nv; v += NT) {
-    const uint32_t l = v * A;
-    const uint64_t i = (base ^ tc.off[l >> tc.C]) | (l & cm);
-    cp_async16(dst + v, g + i / A);
-  }
-}
-
 // ------------------------------------------------------------------ complex helpers
 
 template <typename C2, typename R>
@@ -374,30 +342,16 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3) k_sweep(R *psi, in
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(sizeof(C2), pd, DOUBLE_BUFFER ? 2 : 1, 0);
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, 0);
   const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
-  C2 *tiles = reinterpret_cast<C2 *>(smem + L.tiles);
+  C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   const R sgn = inverse ? (R)-1 : (R)1;
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
-  int cur = 0;
-  if (DOUBLE_BUFFER && blockIdx.x < ntiles) {
-    prefetch_tile<R>(psi, tile_base(blockIdx.x, pd.umask), st, reinterpret_cast<V *>(tiles));
-    cp_async_commit();
-  }
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
-    C2 *tile = tiles + (DOUBLE_BUFFER ? cur * st.amps : 0);
-    if (DOUBLE_BUFFER) {
-      const uint64_t tn = t + gridDim.x;
-      if (tn < ntiles)
-        prefetch_tile<R>(psi, tile_base(tn, pd.umask), st, reinterpret_cast<V *>(tiles + (cur ^ 1) * st.amps));
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tile));
-    }
+    load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tile));
     tile_codes(st, ng, t);
     __syncthreads();
     for (int k = 0; k < nb; ++k) {
@@ -407,9 +361,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3) k_sweep(R *psi, in
     }
     store_tile<R, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
     __syncthreads();
-    cur ^= 1;
   }
-  if (DOUBLE_BUFFER) cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------ reductions
@@ -531,30 +483,16 @@ __global__ void __launch_bounds__(NT, 2) k_expect(const R *psi, int n, PassDesc 
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(sizeof(C2), pd, DOUBLE_BUFFER ? 2 : 1, sizeof(double) * (NT / 32));
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32));
   const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
-  C2 *tiles = reinterpret_cast<C2 *>(smem + L.tiles);
+  C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   double *red = reinterpret_cast<double *>(smem + L.extra);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   Kahan<R> acc_e, acc_n;
-  int cur = 0;
-  if (DOUBLE_BUFFER && blockIdx.x < ntiles) {
-    prefetch_tile<R>(psi, tile_base(blockIdx.x, pd.umask), st, reinterpret_cast<V *>(tiles));
-    cp_async_commit();
-  }
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    C2 *tile = tiles + (DOUBLE_BUFFER ? cur * st.amps : 0);
-    if (DOUBLE_BUFFER) {
-      const uint64_t tn = t + gridDim.x;
-      if (tn < ntiles)
-        prefetch_tile<R>(psi, tile_base(tn, pd.umask), st, reinterpret_cast<V *>(tiles + (cur ^ 1) * st.amps));
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      load_tile<R, STREAM>(psi, tile_base(t, pd.umask), st, reinterpret_cast<V *>(tile));
-    }
+    load_tile<R, STREAM>(psi, tile_base(t, pd.umask), st, reinterpret_cast<V *>(tile));
     tile_codes(st, ng, t);
     __syncthreads();
     if (first_pass) {
@@ -567,9 +505,7 @@ __global__ void __launch_bounds__(NT, 2) k_expect(const R *psi, int n, PassDesc 
     }
     for (int b = 0; b < nb; ++b) expect_block_any<R, TT, GUARD>(tile, st.bs[b], st, acc_e);
     __syncthreads();
-    cur ^= 1;
   }
-  if (DOUBLE_BUFFER) cp_async_wait<0>();
   const double e = block_sum(acc_e.value(), red);
   const double nn = block_sum(acc_n.value(), red);
   if (threadIdx.x == 0) {
@@ -968,7 +904,7 @@ template <typename R>
 cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
                          const BlockDesc *blocks, const void *lut, bool inverse, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
-  const int nvec = DOUBLE_BUFFER ? 2 : 1;
+  const int nvec = 1;
   const size_t smem = smem_layout(sizeof(C2), pd, nvec, 0).total;
   auto k = Q2_DISPATCH(k_sweep, R, n, pd.T);
   cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, 0));
@@ -981,7 +917,7 @@ cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *gro
 template <typename R>
 int expect_grid(int n, int T, int C) {
   using C2 = typename Vec2<R>::type;
-  const int nvec = DOUBLE_BUFFER ? 2 : 1;
+  const int nvec = 1;
   const size_t smem = tile_smem_bytes(sizeof(C2), T, C, nvec);
   auto k = Q2_DISPATCH(k_expect, R, n, T);
   prepare(k, worst_smem(sizeof(C2), T, nvec, sizeof(double) * (NT / 32)));
@@ -993,7 +929,7 @@ cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDe
                           const BlockDesc *blocks, const void *lut, double *partial, int grid, bool first,
                           cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
-  const int nvec = DOUBLE_BUFFER ? 2 : 1;
+  const int nvec = 1;
   const size_t smem = smem_layout(sizeof(C2), pd, nvec, sizeof(double) * (NT / 32)).total;
   auto k = Q2_DISPATCH(k_expect, R, n, pd.T);
   cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, sizeof(double) * (NT / 32)));
