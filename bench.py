@@ -202,6 +202,9 @@ def main():
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad", action="store_true", help="skip the 24-qubit energy+gradient phase")
+    ap.add_argument("--served", type=int, default=48, help="requests in the served-stream phase (0: skip)")
+    ap.add_argument("--served-rate", type=float, default=8.0, help="Poisson arrival rate (requests/s)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -293,15 +296,10 @@ def main():
     e2e = None
     if not args.no_e2e:
         # public API from host arrays: table upload, schedule, LUT, energy read-back, every step
-        for _ in range(1):
-            hh = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
-            aa = q2.Ansatz.from_uccsd(w.ansatz)
-            q2.vqe_energy_grad(aa, hh, theta, dtype=args.dtype, want_grad=False, workspace=work)
-            hh.close()
-            aa.close()
+        e2e_steps = 1
         torch.cuda.synchronize()
         t = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             hh = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
             aa = q2.Ansatz.from_uccsd(w.ansatz)
             q2.vqe_energy_grad(aa, hh, theta, dtype=args.dtype, want_grad=False, workspace=work)
@@ -310,8 +308,13 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - t
         h2d = plan_bytes(lib, w, args.dtype)
-        e2e = {"value": ws * args.steps * units_per_step / wall, "unit": "amp-updates/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16}
+        e2e = {"value": ws * e2e_steps * units_per_step / wall, "unit": "amp-updates/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16, "steps": e2e_steps,
+               "includes": "Hamiltonian and ansatz handles from host arrays (schedules, table uploads), "
+                           "angle LUT upload, all kernels, energy read-back"}
+
+    grad = None if args.no_grad or rank != 0 else grad_phase(q2, torch)
+    served = None if args.served <= 0 or rank != 0 else served_phase(q2, args.served, args.served_rate)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -337,6 +340,8 @@ def main():
             "expectation": {"ms_per_step": expect_ms, "kernels_per_step": int(per[0, 4]),
                             "hbm_gbs_read": float(state_bytes * (per[0, 4] - 1) / (expect_ms / 1000.0) / 1e9)},
             "roofline": roofline,
+            "grad": grad,
+            "served": served,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": gpu_launches,
@@ -346,6 +351,52 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def grad_phase(q2, torch, steps=3):
+    """24 qubits, 12 electrons, 35,136 rotations: complex64 energy + reverse-mode gradient per second."""
+    from synth.workloads import uccsd_energy
+    w = uccsd_energy(24, 12, seed=0)
+    ans = q2.Ansatz.from_uccsd(w.ansatz)
+    ham = q2.Hamiltonian(24, w.ham.x, w.ham.z, w.ham.c)
+    e, g, ws = q2.vqe_energy_grad(ans, ham, w.theta, dtype="complex64", want_grad=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        e, g, ws = q2.vqe_energy_grad(ans, ham, w.theta, dtype="complex64", want_grad=True, workspace=ws)
+    dt = (time.perf_counter() - t) / steps
+    e128, g128, _ = q2.vqe_energy_grad(ans, ham, w.theta, dtype="complex128", want_grad=True)
+    return {"workload": "24 qubits, 12 electrons, 35136 rotations over 4500 parameters, energy + dE/dtheta",
+            "evals_per_s": 1.0 / dt, "ms_per_eval": 1000.0 * dt, "energy": e,
+            "abs_dE_vs_complex128": abs(e - e128), "max_abs_dgrad_vs_complex128": float(np.max(np.abs(g - g128)))}
+
+
+def served_phase(q2, n_requests, rate):
+    """Bounded Poisson stream through the serving loop (10..26 qubits, 40% with gradient, 150 GB budget)."""
+    from paper_2208_10978_gb300 import serve
+    from synth.workloads import served_stream, uccsd_energy
+    reqs = served_stream(seed=0, n_requests=n_requests, rate_per_s=rate)
+    problems, thetas = {}, {}
+    t = time.perf_counter()
+    for r in reqs:
+        if r.problem_seed not in problems:
+            w = uccsd_energy(r.n, r.n_elec, seed=r.problem_seed % 100000)
+            problems[r.problem_seed] = serve.problem_from_workload(w, key=r.problem_seed)
+            thetas[r.problem_seed] = w.theta
+    gen_s = time.perf_counter() - t
+    srv = serve.Server(dtype="complex64", budget_bytes=150 * 10**9, max_slots=64, n_streams=4)
+    try:
+        results, wall = serve.serve_stream(srv, reqs, problems, thetas, wait_s=900)
+        st = srv.stats()
+    finally:
+        srv.close()
+    ok = [r for r in results.values() if r.status == 0]
+    grad_ok = [r for r in ok if r.grad is not None]
+    return {"requests": len(reqs), "completed": len(ok), "with_grad": len(grad_ok),
+            "arrival_rate_per_s": rate, "evals_per_s": len(ok) / wall, "wall_s": wall,
+            "p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"], "mean_latency_s": st["mean_s"],
+            "hbm_high_water_bytes": st["high_water_bytes"], "budget_bytes": 150 * 10**9,
+            "dtype": "c64 state, f64 reductions", "problem_generation_s_excluded": gen_s}
 
 
 def plan_bytes(lib, w, dtype):
