@@ -50,6 +50,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device="cpu"):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, units_per_step, max_ms):
+    """Units all replicas processed per second of the slowest rank's time."""
+    return world * steps * units_per_step / (max_ms / 1000.0)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -268,14 +283,10 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tmax = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms = float(tmax.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     per = np.array(per)
     units_per_step = float(w.ansatz.n_rot) * float(1 << n)
-    value = ws * args.steps * units_per_step / (ms / 1000.0)
+    value = whole_job_rate(ws, args.steps, units_per_step, ms)
 
     # dominant kernel: the sweep pass (k_sweep), HBM-bound for complex64
     state_bytes = float(per[0, 7])
@@ -306,9 +317,9 @@ def main():
             hh.close()
             aa.close()
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t
+        wall = max_over_ranks(time.perf_counter() - t, dist, "cuda")
         h2d = plan_bytes(lib, w, args.dtype)
-        e2e = {"value": ws * e2e_steps * units_per_step / wall, "unit": "amp-updates/s",
+        e2e = {"value": whole_job_rate(ws, e2e_steps, units_per_step, 1000.0 * wall), "unit": "amp-updates/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16, "steps": e2e_steps,
                "includes": "Hamiltonian and ansatz handles from host arrays (schedules, table uploads), "
                            "angle LUT upload, all kernels, energy read-back"}
