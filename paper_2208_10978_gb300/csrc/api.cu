@@ -273,7 +273,7 @@ template <typename R>
 cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups, const BlockDesc *dblocks,
                       const void *dlut, cudaStream_t st) {
   for (const PassDesc &pd : p.passes) {
-    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dblocks, dlut, false, st);
+    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dblocks, dlut, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -17,7 +17,7 @@
 // from host tables plus one per-tile code per group.
 //
 //   k_init_hf     HF determinant (Eq. jw-wfn-map)
-//   k_sweep       rotation groups, forward or inverse (product formula after Eq. ucc)
+//   k_sweep       rotation groups in order (product formula after Eq. ucc)
 //   k_expect      sum_t c_t <psi|P_t|psi> and <psi|psi> (Eq. qubit-ham-detail)
 //   k_happly      lambda = H psi (Algorithm 1, start of the backward pass)
 //   k_dot         Re<psi|lambda>, <psi|psi>
@@ -65,7 +65,8 @@ struct SmemLayout {
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc &pd, int vectors,
-                                                  size_t extra_bytes) {
+                                                  size_t extra_bytes, int lut_entry_bytes = 0) {
+  if (lut_entry_bytes == 0) lut_entry_bytes = amp_bytes;
   SmemLayout L;
   size_t o = 0;
   L.tiles = o;
@@ -77,7 +78,7 @@ __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc 
   L.blocks = o;
   o = align16(o + sizeof(BlockDesc) * (size_t)(pd.b_end - pd.b_begin));
   L.lut = o;
-  o = align16(o + (size_t)amp_bytes * (size_t)pd.lut_count);
+  o = align16(o + (size_t)lut_entry_bytes * (size_t)pd.lut_count);
   L.tcode = o;
   o = align16(o + sizeof(uint32_t) * (size_t)(pd.g_end - pd.g_begin));
   L.extra = o;
@@ -86,14 +87,31 @@ __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc 
   return L;
 }
 
-template <typename R> struct Stage {
+// LUT entry of the forward sweep in shared memory.  complex64 with packed
+// FP32 pair arithmetic keeps (cos, cos, sin, sin) so both packed operands
+// come from one 16-byte load; otherwise (cos, sin).
+#ifndef Q2_F32X2
+#define Q2_F32X2 1
+#endif
+template <typename R> struct SweepLut { using E = typename Vec2<R>::type; };
+#if Q2_F32X2
+template <> struct SweepLut<float> { using E = float4; };
+#endif
+__device__ __forceinline__ float lut_cos(float2 e) { return e.x; }
+__device__ __forceinline__ float lut_sin(float2 e) { return e.y; }
+__device__ __forceinline__ double lut_cos(double2 e) { return e.x; }
+__device__ __forceinline__ double lut_sin(double2 e) { return e.y; }
+__device__ __forceinline__ float lut_cos(float4 e) { return e.x; }
+__device__ __forceinline__ float lut_sin(float4 e) { return e.z; }
+
+template <typename R, typename E = typename Vec2<R>::type> struct Stage {
   using C2 = typename Vec2<R>::type;
   int T, C;
   uint32_t amps;
   uint64_t *off;
   const GroupDesc *gs;   // staged groups of the pass (index g - g_begin)
   const BlockDesc *bs;   // staged blocks of the pass (index b - b_begin)
-  const C2 *lut;         // staged LUT, indexed by the global LUT offset
+  const E *lut;          // staged LUT, indexed by the global LUT offset
   uint32_t *tcode;       // per-tile code of each group
 };
 
@@ -106,13 +124,13 @@ __device__ __forceinline__ void copy16(void *dst, const T *src, int count) {
 }
 
 // Stage offsets, descriptors and LUT of a pass; caller syncs.
-template <typename R>
-__device__ __forceinline__ Stage<R> stage_pass(unsigned char *smem, const PassDesc &pd,
-                                               const SmemLayout &L, const GroupDesc *groups,
-                                               const BlockDesc *blocks,
-                                               const typename Vec2<R>::type *lut) {
+template <typename R, typename E = typename Vec2<R>::type>
+__device__ __forceinline__ Stage<R, E> stage_pass(unsigned char *smem, const PassDesc &pd,
+                                                  const SmemLayout &L, const GroupDesc *groups,
+                                                  const BlockDesc *blocks,
+                                                  const typename Vec2<R>::type *lut) {
   using C2 = typename Vec2<R>::type;
-  Stage<R> t;
+  Stage<R, E> t;
   t.T = pd.T;
   t.C = pd.C;
   t.amps = 1u << pd.T;
@@ -126,8 +144,12 @@ __device__ __forceinline__ Stage<R> stage_pass(unsigned char *smem, const PassDe
   }
   copy16(smem + L.groups, groups + pd.g_begin, pd.g_end - pd.g_begin);
   if (blocks) copy16(smem + L.blocks, blocks + pd.b_begin, pd.b_end - pd.b_begin);
-  C2 *ld = reinterpret_cast<C2 *>(smem + L.lut);
-  for (int i = threadIdx.x; i < pd.lut_count; i += NT) ld[i] = __ldg(lut + pd.lut_begin + i);
+  E *ld = reinterpret_cast<E *>(smem + L.lut);
+  for (int i = threadIdx.x; i < pd.lut_count; i += NT) {
+    const C2 e = __ldg(lut + pd.lut_begin + i);
+    if constexpr (sizeof(E) == sizeof(C2)) ld[i] = e;
+    else ld[i] = E{e.x, e.x, e.y, e.y};
+  }
   t.gs = reinterpret_cast<const GroupDesc *>(smem + L.groups);
   t.bs = reinterpret_cast<const BlockDesc *>(smem + L.blocks);
   t.lut = ld - pd.lut_begin;
@@ -136,8 +158,8 @@ __device__ __forceinline__ Stage<R> stage_pass(unsigned char *smem, const PassDe
 }
 
 // Tile part of every group's code for tile t (threads g < ng); caller syncs.
-template <typename R>
-__device__ __forceinline__ void tile_codes(const Stage<R> &s, int ng, uint64_t t) {
+template <typename R, typename E>
+__device__ __forceinline__ void tile_codes(const Stage<R, E> &s, int ng, uint64_t t) {
   const int g = threadIdx.x;
   if (g < ng) {
     const GroupDesc &d = s.gs[g];
@@ -155,8 +177,8 @@ __device__ __forceinline__ uint64_t tile_base(uint64_t t, uint64_t umask) { retu
 #define Q2_LOAD_BATCH 4
 #endif
 constexpr int LOAD_BATCH = Q2_LOAD_BATCH;
-template <typename R, bool STREAM>
-__device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Stage<R> &tc,
+template <typename R, bool STREAM, typename E>
+__device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Stage<R, E> &tc,
                                           typename Vec16<R>::type *dst) {
   using V = typename Vec16<R>::type;
   constexpr int A = Vec16<R>::amps;
@@ -182,8 +204,8 @@ __device__ __forceinline__ void load_tile(const R *src, uint64_t base, const Sta
   }
 }
 
-template <typename R, bool STREAM>
-__device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Stage<R> &tc,
+template <typename R, bool STREAM, typename E>
+__device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Stage<R, E> &tc,
                                            const typename Vec16<R>::type *src) {
   using V = typename Vec16<R>::type;
   constexpr int A = Vec16<R>::amps;
@@ -218,6 +240,47 @@ __device__ __forceinline__ void phase(C2 &a, R c, R s) {               // (c - i
   a = C2{c * x.x + s * x.y, c * x.y - s * x.x};
 }
 
+// Packed FP32 pairs: one instruction updates (re, im) of an amplitude.
+__device__ __forceinline__ unsigned long long f2_pack(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// [[c, -s], [s, c]] on (a, b) with e = (c, c, s, s).
+__device__ __forceinline__ void rot_real(float2 &a, float2 &b, float4 e) {
+  const unsigned long long A = f2_pack(a.x, a.y), B = f2_pack(b.x, b.y);
+  const unsigned long long C = f2_pack(e.x, e.y), S = f2_pack(e.z, e.w);
+  const unsigned long long na = f2_sub(f2_mul(C, A), f2_mul(S, B));
+  const unsigned long long nb = f2_fma(S, A, f2_mul(C, B));
+  a = f2_unpack(na);
+  b = f2_unpack(nb);
+}
+template <typename C2, typename E>
+__device__ __forceinline__ void rot_real(C2 &a, C2 &b, E e) {
+  rot_real(a, b, lut_cos(e), lut_sin(e));
+}
+
 // ------------------------------------------------------------------ init
 
 template <typename R>
@@ -244,41 +307,44 @@ template <int TT, int D> struct BlockShape {
   static constexpr int N = 1 << D;
 };
 
-// Rotate the pairs (c, c ^ A) of a coset held in registers.
-template <typename R, int D, int A>
-__device__ __forceinline__ void coset_pairs(typename Vec2<R>::type (&v)[1 << D], const GroupDesc &g,
-                                            const typename Vec2<R>::type *L, uint32_t cb, R sgn,
-                                            bool real) {
+// Rotate the pairs (c, c ^ A) of a coset held in registers.  REAL: the pair
+// update [[c, -s], [s, c]]; otherwise c - i s X.
+template <typename R, int D, int A, bool REAL, typename E>
+__device__ __forceinline__ void coset_pairs(typename Vec2<R>::type (&v)[1 << D], const uint32_t (&bw)[4],
+                                            const E *L, uint32_t cb) {
   constexpr int HB = 31 - __builtin_clz(A);
-  const uint4 b4 = *reinterpret_cast<const uint4 *>(g.bccode);   // all combo codes in one load
-  const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
   for (int c = 0; c < (1 << D); ++c) {
     if ((c >> HB) & 1) continue;
-    const auto cs = L[cb ^ ((bw[c >> 2] >> (8 * (c & 3))) & 0xffu)];
-    if (real) rot_real(v[c], v[c ^ A], cs.x, sgn * cs.y);
-    else rot_xrot(v[c], v[c ^ A], cs.x, sgn * cs.y);
+    const uint32_t code = (bw[c >> 2] >> (8 * (c & 3))) & 0xffu;   // combo c's code byte
+    const E cs = L[cb ^ code];
+    if (REAL) rot_real(v[c], v[c ^ A], cs);
+    else rot_xrot(v[c], v[c ^ A], lut_cos(cs), lut_sin(cs));
   }
 }
 
-template <typename R, int D, int A>
-__device__ __forceinline__ void coset_pairs_any(int a, typename Vec2<R>::type (&v)[1 << D],
-                                                const GroupDesc &g, const typename Vec2<R>::type *L,
-                                                uint32_t cb, R sgn, bool real) {
-  if constexpr (A < (1 << D)) {
-    if (a == A) {
-      coset_pairs<R, D, A>(v, g, L, cb, sgn, real);
-      return;
-    }
-    coset_pairs_any<R, D, A + 1>(a, v, g, L, cb, sgn, real);
+// One jump on the pair offset a (1 .. 2^D - 1) into the unrolled pair loop.
+template <typename R, int D, bool REAL, typename E>
+__device__ __forceinline__ void coset_pairs_sw(int a, typename Vec2<R>::type (&v)[1 << D],
+                                               const uint32_t (&bw)[4], const E *L, uint32_t cb) {
+  switch (a) {
+#define Q2_PC(X) \
+  case X:        \
+    if constexpr (X < (1 << D)) coset_pairs<R, D, X, REAL, E>(v, bw, L, cb); \
+    break;
+    Q2_PC(1) Q2_PC(2) Q2_PC(3) Q2_PC(4) Q2_PC(5) Q2_PC(6) Q2_PC(7) Q2_PC(8)
+    Q2_PC(9) Q2_PC(10) Q2_PC(11) Q2_PC(12) Q2_PC(13) Q2_PC(14) Q2_PC(15)
+#undef Q2_PC
+    default: break;
   }
 }
 
 // One register block of the sweep.  J cosets per thread (GUARD: at most one).
 template <typename R, int D, int J, bool GUARD>
 __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const BlockDesc &B,
-                                            const Stage<R> &s, R sgn, bool inverse) {
+                                            const Stage<R, typename SweepLut<R>::E> &s) {
   using C2 = typename Vec2<R>::type;
+  using E = typename SweepLut<R>::E;
   constexpr int N = 1 << D;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (GUARD && tid >= (s.amps >> D)) return;
@@ -292,19 +358,24 @@ __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const 
     C2 v[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
-    for (int k = 0; k < ge - gb; ++k) {
-      const int gi = inverse ? ge - 1 - k : gb + k;
+#pragma unroll 1
+    for (int gi = gb; gi < ge; ++gi) {
       const GroupDesc &g = s.gs[gi];
       const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
-      const C2 *L = s.lut + g.lut;
-      if (g.kind == KIND_DIAG) {
+      const E *L = s.lut + g.lut;
+      const uint4 b4 = *reinterpret_cast<const uint4 *>(g.bccode);   // all combo codes in one load
+      const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
+      const int kind = g.kind;
+      if (kind == KIND_REAL) {
+        coset_pairs_sw<R, D, true, E>(g.a, v, bw, L, cb);
+      } else if (kind == KIND_DIAG) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-          const C2 cs = L[cb ^ g.bccode[c]];
-          phase(v[c], cs.x, sgn * cs.y);
+          const E cs = L[cb ^ g.bccode[c]];
+          phase(v[c], lut_cos(cs), lut_sin(cs));
         }
       } else {
-        coset_pairs_any<R, D, 1>(g.a, v, g, L, cb, sgn, g.kind == KIND_REAL);
+        coset_pairs_sw<R, D, false, E>(g.a, v, bw, L, cb);
       }
     }
 #pragma unroll
@@ -314,20 +385,20 @@ __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const 
 
 template <typename R, int TT, bool GUARD>
 __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, const BlockDesc &B,
-                                                const Stage<R> &s, R sgn, bool inverse) {
+                                                const Stage<R, typename SweepLut<R>::E> &s) {
   if constexpr (GUARD) {
-    sweep_block<R, 1, 1, true>(tile, B, s, sgn, inverse);
+    sweep_block<R, 1, 1, true>(tile, B, s);
   } else {
     switch (B.d) {
-      case 1: sweep_block<R, 1, BlockShape<TT, 1>::J, false>(tile, B, s, sgn, inverse); break;
+      case 1: sweep_block<R, 1, BlockShape<TT, 1>::J, false>(tile, B, s); break;
       case 2:
-        if constexpr (TT >= 10) sweep_block<R, 2, BlockShape<TT, 2>::J, false>(tile, B, s, sgn, inverse);
+        if constexpr (TT >= 10) sweep_block<R, 2, BlockShape<TT, 2>::J, false>(tile, B, s);
         break;
       case 3:
-        if constexpr (TT >= 11) sweep_block<R, 3, BlockShape<TT, 3>::J, false>(tile, B, s, sgn, inverse);
+        if constexpr (TT >= 11) sweep_block<R, 3, BlockShape<TT, 3>::J, false>(tile, B, s);
         break;
       case 4:
-        if constexpr (TT >= 12) sweep_block<R, 4, BlockShape<TT, 4>::J, false>(tile, B, s, sgn, inverse);
+        if constexpr (TT >= 12) sweep_block<R, 4, BlockShape<TT, 4>::J, false>(tile, B, s);
         break;
     }
   }
@@ -336,27 +407,26 @@ __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, co
 // ------------------------------------------------------------------ rotation sweep
 
 template <typename R, bool STREAM, int TT, bool GUARD>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3) k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups,
-                                                 const BlockDesc *blocks,
-                                                 const typename Vec2<R>::type *lut, int inverse) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
+    k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups, const BlockDesc *blocks,
+            const typename Vec2<R>::type *lut) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, 0);
-  const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
+  using E = typename SweepLut<R>::E;
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, 0, sizeof(E));
+  const Stage<R, E> st = stage_pass<R, E>(smem, pd, L, groups, blocks, lut);
   C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
-  const R sgn = inverse ? (R)-1 : (R)1;
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tile_base(t, pd.umask);
     load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tile));
     tile_codes(st, ng, t);
     __syncthreads();
-    for (int k = 0; k < nb; ++k) {
-      const int b = inverse ? nb - 1 - k : k;
-      sweep_block_any<R, TT, GUARD>(tile, st.bs[b], st, sgn, inverse != 0);
+    for (int b = 0; b < nb; ++b) {
+      sweep_block_any<R, TT, GUARD>(tile, st.bs[b], st);
       __syncthreads();
     }
     store_tile<R, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
@@ -393,41 +463,60 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 
 // ------------------------------------------------------------------ expectation
 
-template <typename R, int D, int A>
-__device__ __forceinline__ R coset_expect(const typename Vec2<R>::type (&v)[1 << D], const GroupDesc &g,
+// sum over the pairs (c, c ^ A) of a coset of R Re w + Q Im w, w = conj(v_c) v_{c^A},
+// (R, Q) = L[cb ^ code(c)]; the caller doubles it (each pair counts i<j and j>i).
+// QZERO: the group's Q vanishes at every code (real pair coefficients).
+template <typename R, int D, int A, bool QZERO>
+__device__ __forceinline__ R coset_expect(const typename Vec2<R>::type (&v)[1 << D], uint2 b2,
                                           const typename Vec2<R>::type *L, uint32_t cb) {
   constexpr int HB = 31 - __builtin_clz(A);
-  const uint2 b2 = *reinterpret_cast<const uint2 *>(g.bccode);   // combo codes c < 8 in one load
   const uint32_t bw[2] = {b2.x, b2.y};
   R s = 0;
 #pragma unroll
   for (int c = 0; c < (1 << D); ++c) {
     if ((c >> HB) & 1) continue;
-    const auto rq = L[cb ^ ((bw[c >> 2] >> (8 * (c & 3))) & 0xffu)];
+    const uint32_t idx = cb ^ ((bw[c >> 2] >> (8 * (c & 3))) & 0xffu);
     const auto a = v[c], b = v[c ^ A];
-    // w = conj(a) b ; contribution 2 (R Re w + Q Im w), factor 2 applied by the caller
-    s += rq.x * (a.x * b.x + a.y * b.y) + rq.y * (a.x * b.y - a.y * b.x);
+    if constexpr (QZERO) {
+      s += L[idx].x * (a.x * b.x + a.y * b.y);
+    } else {
+      const auto rq = L[idx];
+      s += rq.x * (a.x * b.x + a.y * b.y) + rq.y * (a.x * b.y - a.y * b.x);
+    }
   }
   return s;
 }
 
-template <typename R, int D, int A>
-__device__ __forceinline__ R coset_expect_any(int a, const typename Vec2<R>::type (&v)[1 << D],
-                                              const GroupDesc &g, const typename Vec2<R>::type *L,
-                                              uint32_t cb) {
-  if constexpr (A < (1 << D)) {
-    if (a == A) return coset_expect<R, D, A>(v, g, L, cb);
-    return coset_expect_any<R, D, A + 1>(a, v, g, L, cb);
-  } else {
-    return (R)0;
+// e[j] += 2 * coset_expect(v[j]) for every coset of a chunk; one jump on a.
+template <typename R, int D, int JC, bool QZERO>
+__device__ __forceinline__ void chunk_expect(int a, const typename Vec2<R>::type (&v)[JC][1 << D], R (&e)[JC],
+                                             uint2 b2, const typename Vec2<R>::type *L, uint32_t cb,
+                                             const uint8_t *bjcode) {
+  switch (a) {
+#define Q2_EC(X)                                                              \
+  case X:                                                                     \
+    if constexpr (X < (1 << D)) {                                             \
+      _Pragma("unroll") for (int j = 0; j < JC; ++j)                          \
+        e[j] += 2 * coset_expect<R, D, X, QZERO>(v[j], b2, L, cb ^ bjcode[j]); \
+    }                                                                         \
+    break;
+    Q2_EC(1) Q2_EC(2) Q2_EC(3) Q2_EC(4) Q2_EC(5) Q2_EC(6) Q2_EC(7)
+#undef Q2_EC
+    default: break;
   }
 }
 
+// One register block of the expectation.  The thread's J cosets are taken in
+// chunks of JC (JC * 2^D amplitudes in registers); for each chunk it walks the
+// block's groups once.  Each coset's contribution is summed over the groups in
+// the state precision and enters the compensated accumulator once per block.
 template <typename R, int D, int J, bool GUARD>
 __device__ __forceinline__ void expect_block(const typename Vec2<R>::type *tile, const BlockDesc &B,
                                              const Stage<R> &s, Kahan<R> &acc) {
   using C2 = typename Vec2<R>::type;
   constexpr int N = 1 << D;
+  constexpr int AMPS = 8;   // amplitudes a thread keeps in registers per chunk
+  constexpr int JC = J < AMPS / N ? J : (AMPS / N > 0 ? AMPS / N : 1);
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (GUARD && tid >= (s.amps >> D)) return;
   uint32_t bt = tid;
@@ -435,24 +524,38 @@ __device__ __forceinline__ void expect_block(const typename Vec2<R>::type *tile,
   for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
   const int gb = B.g_begin, ge = B.g_end;
 #pragma unroll 1
-  for (int j = 0; j < J; ++j) {
-    const uint32_t bj = bt ^ B.uj[j];
-    C2 v[N];
+  for (int j0 = 0; j0 < J; j0 += JC) {
+    C2 v[JC][N];
 #pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
+    for (int j = 0; j < JC; ++j) {
+      const uint32_t bj = bt ^ B.uj[j0 + j];
+#pragma unroll
+      for (int c = 0; c < N; ++c) v[j][c] = tile[bj ^ B.comb[c]];
+    }
+    R e[JC];
+#pragma unroll
+    for (int j = 0; j < JC; ++j) e[j] = 0;
+#pragma unroll 1
     for (int gi = gb; gi < ge; ++gi) {
       const GroupDesc &g = s.gs[gi];
-      const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
+      const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp];
       const C2 *L = s.lut + g.lut;
-      R e = 0;
       if (g.kind == KIND_DIAG) {
 #pragma unroll
-        for (int c = 0; c < N; ++c) e += L[cb ^ g.bccode[c]].x * (v[c].x * v[c].x + v[c].y * v[c].y);
+        for (int j = 0; j < JC; ++j) {
+          const uint32_t cj = cb ^ g.bjcode[j0 + j];
+#pragma unroll
+          for (int c = 0; c < N; ++c)
+            e[j] += L[cj ^ g.bccode[c]].x * (v[j][c].x * v[j][c].x + v[j][c].y * v[j][c].y);
+        }
       } else {
-        e = 2 * coset_expect_any<R, D, 1>(g.a, v, g, L, cb);
+        const uint2 b2 = *reinterpret_cast<const uint2 *>(g.bccode);   // combo codes c < 8 in one load
+        if (g.kind == KIND_REAL) chunk_expect<R, D, JC, true>(g.a, v, e, b2, L, cb, g.bjcode + j0);
+        else chunk_expect<R, D, JC, false>(g.a, v, e, b2, L, cb, g.bjcode + j0);
       }
-      acc.add(e);
     }
+#pragma unroll
+    for (int j = 0; j < JC; ++j) acc.add(e[j]);
   }
 }
 
@@ -470,7 +573,6 @@ __device__ __forceinline__ void expect_block_any(const typename Vec2<R>::type *t
       case 3:
         if constexpr (TT >= 11) expect_block<R, 3, BlockShape<TT, 3>::J, false>(tile, B, s, acc);
         break;
-
     }
   }
 }
@@ -598,6 +700,7 @@ __global__ void __launch_bounds__(NT, 3) k_happly(const R *psi, R *lam, int n, P
       } else if (!GUARD || tid < (st.amps >> 1)) {
         const uint32_t li0 = insert_zero(tid, d.pivot);
         const uint32_t xl = d.xl;
+        const bool qzero = d.kind == KIND_REAL;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
           const uint32_t li = li0 | d.pu[j], lj = li ^ xl;
@@ -605,10 +708,17 @@ __global__ void __launch_bounds__(NT, 3) k_happly(const R *psi, R *lam, int n, P
           const C2 a = tp[li], b = tp[lj];
           C2 oi = tl[li], oj = tl[lj];
           // lam_i += (R - iQ) psi_j ; lam_j += (R + iQ) psi_i
-          oi.x += rq.x * b.x + rq.y * b.y;
-          oi.y += rq.x * b.y - rq.y * b.x;
-          oj.x += rq.x * a.x - rq.y * a.y;
-          oj.y += rq.x * a.y + rq.y * a.x;
+          if (qzero) {
+            oi.x += rq.x * b.x;
+            oi.y += rq.x * b.y;
+            oj.x += rq.x * a.x;
+            oj.y += rq.x * a.y;
+          } else {
+            oi.x += rq.x * b.x + rq.y * b.y;
+            oi.y += rq.x * b.y - rq.y * b.x;
+            oj.x += rq.x * a.x - rq.y * a.y;
+            oj.y += rq.x * a.y + rq.y * a.x;
+          }
           tl[li] = oi;
           tl[lj] = oj;
         }
@@ -808,7 +918,8 @@ int blocks_per_sm(K kernel, size_t smem) {
 // (tile size T, smallest chunk, fullest staged tables).  The attribute is
 // per-function state shared by every host thread, so it is always set to this
 // fixed value, never to one launch's size.
-size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra) {
+size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry_bytes = 0) {
+  if (lut_entry_bytes == 0) lut_entry_bytes = amp_bytes;
   PassDesc pd{};
   pd.T = T <= 8 ? 8 : T;
   pd.C = 1;
@@ -823,7 +934,7 @@ size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra) {
   o = align16(o + sizeof(uint64_t) * ((size_t)1 << (pd.T - pd.C)));
   o = align16(o + sizeof(GroupDesc) * G_STAGE);
   o = align16(o + sizeof(BlockDesc) * G_STAGE);
-  o = align16(o + (size_t)amp_bytes * LUT_STAGE);
+  o = align16(o + (size_t)lut_entry_bytes * LUT_STAGE);
   o = align16(o + sizeof(uint32_t) * G_STAGE);
   o = align16(o + extra);
   (void)L;
@@ -902,15 +1013,16 @@ cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st) {
 
 template <typename R>
 cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                         const BlockDesc *blocks, const void *lut, bool inverse, cudaStream_t st) {
+                         const BlockDesc *blocks, const void *lut, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const int nvec = 1;
-  const size_t smem = smem_layout(sizeof(C2), pd, nvec, 0).total;
+  const int eb = (int)sizeof(typename SweepLut<R>::E);
+  const size_t smem = smem_layout(sizeof(C2), pd, nvec, 0, eb).total;
   auto k = Q2_DISPATCH(k_sweep, R, n, pd.T);
-  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, 0));
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, 0, eb));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
-  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), inverse ? 1 : 0);
+  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut));
   return cudaGetLastError();
 }
 
@@ -996,7 +1108,7 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
 #define Q2_INST(R)                                                                                  \
   template cudaError_t launch_init_hf<R>(R *, int, int, cudaStream_t);                             \
   template cudaError_t launch_sweep<R>(R *, int, const PassDesc &, const GroupDesc *,              \
-                                       const BlockDesc *, const void *, bool, cudaStream_t);        \
+                                       const BlockDesc *, const void *, cudaStream_t);              \
   template int expect_grid<R>(int, int, int);                                                       \
   template cudaError_t launch_expect<R>(const R *, int, const PassDesc &, const GroupDesc *,        \
                                         const BlockDesc *, const void *, double *, int, bool,       \

@@ -15,7 +15,7 @@ cudaError_t launch_reduce_pairs(const double *partial, int nblocks, double *out,
 template <typename R> cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                         const BlockDesc *blocks, const void *lut, bool inverse, cudaStream_t st);
+                         const BlockDesc *blocks, const void *lut, cudaStream_t st);
 template <typename R> int expect_grid(int n, int T, int C);
 template <typename R>
 cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDesc *groups,

@@ -45,6 +45,10 @@ constexpr int LUT_STAGE = 1024;  // max LUT entries per pass (staged in shared m
 constexpr int T_MIN = 8;
 constexpr int T_LIMIT = 13;
 
+// Group kinds.  Rotation groups: DIAG (x = 0, a phase per code), REAL (odd
+// Y count: real 2x2 rotation of each pair), XROT (even Y count: c - i s X).
+// Hamiltonian groups: DIAG, REAL (every member has an even Y count, so the
+// pair coefficient R - iQ is real: Q = 0 at every code) and PAIR (general).
 enum : uint8_t { KIND_DIAG = 0, KIND_REAL = 1, KIND_XROT = 2, KIND_PAIR = 3 };
 
 constexpr int D_MAX = 4;         // max span dimension of a register block (rotations)

@@ -222,18 +222,22 @@ void form_blocks(std::vector<GroupDesc> &groups, size_t first, size_t last, int 
       if (xl) span.add(xl);
       ++e;
     }
-    // reduced echelon basis of the span (pivot = highest bit, no other pivot bits)
-    std::vector<uint64_t> v = span.red;   // distinct highest bits
-    if (v.empty()) v.push_back(1);        // diagonal-only block: any one local direction
-    std::sort(v.begin(), v.end(), [](uint64_t a, uint64_t b) { return high_bit(a) < high_bit(b); });
-    // clear every pivot from the other rows, lowest pivot first (no bit comes back)
-    for (size_t i = 0; i < v.size(); ++i)
-      for (size_t k = 0; k < v.size(); ++k)
-        if (k != i && ((v[k] >> high_bit(v[i])) & 1)) v[k] ^= v[i];
+    // Basis of the block: the groups' own xmasks in order of appearance, so a
+    // group that opens a new dimension pairs combos along one basis bit.
+    // Pivots are the highest bits of the echelon rows: the basis restricted
+    // to them is invertible, so base(s) ^ comb[c] enumerates the tile once.
+    std::vector<uint64_t> v = span.orig;
+    std::vector<int> piv;
+    for (uint64_t r : span.red) piv.push_back(high_bit(r));
+    if (v.empty()) {                      // diagonal-only block: any one local direction
+      v.push_back(1);
+      piv.push_back(0);
+    }
+    std::sort(piv.begin(), piv.end());
     BlockDesc b;
     std::memset(&b, 0, sizeof(b));
     b.d = (uint8_t)v.size();
-    for (int i = 0; i < b.d; ++i) b.piv[i] = (uint8_t)high_bit(v[i]);
+    for (int i = 0; i < b.d; ++i) b.piv[i] = (uint8_t)piv[i];
     for (uint32_t c = 0; c < (1u << b.d); ++c) {
       uint64_t o = 0;
       for (int i = 0; i < b.d; ++i)
@@ -248,16 +252,8 @@ void form_blocks(std::vector<GroupDesc> &groups, size_t first, size_t last, int 
     b.g_end = (uint16_t)(e - first);
     for (size_t k = g; k < e; ++k) {
       GroupDesc &d = groups[k];
-      // coordinates of xl in the basis v (v is in reduced echelon form)
-      uint32_t a = 0;
-      uint64_t rem = d.xl;
-      for (int i = b.d - 1; i >= 0; --i)
-        if ((rem >> b.piv[i]) & 1) {
-          rem ^= v[i];
-          a |= 1u << i;
-        }
-      if (rem != 0) throw std::logic_error("group xmask outside its block span");
-      d.a = (uint8_t)a;
+      // coordinates of xl in the basis v
+      d.a = d.xl ? (uint8_t)span.coords(d.xl) : (uint8_t)0;
       for (uint32_t c = 0; c < (1u << b.d); ++c) d.bccode[c] = (uint8_t)local_code(d, b.comb[c], T);
       for (int64_t j = 0; j < J; ++j) d.bjcode[j] = (uint8_t)local_code(d, b.uj[j], T);
       for (int lane = 0; lane < 32; ++lane) d.blane[lane] = (uint8_t)local_code(d, block_base(lane, b), T);
@@ -568,6 +564,11 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
     for (size_t g : pass_groups[p]) {
       const RawGroup &rg = groups[g];
       GroupDesc d = make_desc(rg, tl, lut);
+      // Every member with an even Y count gives a real pair coefficient
+      // (Q = 0 at every code): such groups run the real-coefficient path.
+      bool any_odd = false;
+      for (int64_t t : rg.members) any_odd |= (popc64(x[t] & z[t]) & 1) != 0;
+      if (d.kind == KIND_PAIR && !any_odd) d.kind = KIND_REAL;
       H.groups.push_back(d);
       const uint32_t ncode = 1u << d.r;
       H.lut2.resize(2 * (size_t)(lut + ncode), 0.0);

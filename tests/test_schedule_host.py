@@ -169,6 +169,25 @@ def test_schedule_chemistry_hamiltonian(lib):
     assert abs(e - sv.expectation(psi, w.ham.x, w.ham.z, w.ham.c)) < 1e-11
 
 
+def test_real_coefficient_groups(lib):
+    """Groups whose members all have an even Y count are marked real and have Q = 0;
+    a group with an odd-Y member keeps the general kind."""
+    w = uccsd_energy(10, 5, seed=2)
+    passes, groups, blocks, lut = emu.ham_plan(lib, 10, w.ham.x, w.ham.z, w.ham.c, 8, 4)
+    off = groups[groups["kind"] != emu.DIAG]
+    assert len(off) > 0 and np.all(off["kind"] == emu.REAL)
+    for g in off:
+        assert np.all(lut[int(g["lut"]):int(g["lut"]) + (1 << int(g["r"])), 1] == 0.0)
+    x = np.array([3, 3, 5], dtype=np.uint64)
+    z = np.array([1, 0, 4], dtype=np.uint64)      # (X Y), (X X): one odd-Y member; (X Z Y) alone
+    passes, groups, blocks, lut = emu.ham_plan(lib, 4, x, z, np.array([0.5, 0.25, 1.0]), 4, 1)
+    kinds = {int(g["xl"]): int(g["kind"]) for g in groups}
+    assert sorted(kinds.values()) == [emu.PAIR, emu.PAIR]
+    psi = np.random.default_rng(1).normal(size=16) + 1j * np.random.default_rng(2).normal(size=16)
+    e, _ = emu.expectation(psi, 4, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta())
+    assert abs(e - sv.expectation(psi, x, z, [0.5, 0.25, 1.0])) < 1e-12
+
+
 @pytest.mark.parametrize("n,ne,T,C", [(8, 4, 6, 2), (10, 4, 7, 3)])
 def test_schedule_reverse_gradient(lib, n, ne, T, C):
     w = uccsd_energy(n, ne, seed=4)
