@@ -219,7 +219,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the 24-qubit energy+gradient phase")
     ap.add_argument("--served", type=int, default=48, help="requests in the served-stream phase (0: skip)")
-    ap.add_argument("--served-rate", type=float, default=8.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--served-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 

@@ -16,7 +16,7 @@
  *            bccode[16], blane[32], bwarp[8] (register-block enumeration);
  *            uint8 pivot, pad[7], pjcode[32], plane[32], pwarp[8]; uint16 pu[16]
  *            (pair enumeration); uint8 pad[8].
- *   q2_block (80 bytes): uint16 comb[16], uj[16]; uint8 d, piv[4], pad[3];
+ *   q2_block (80 bytes): uint16 comb[16], uj[16]; uint8 d, piv[4], canon, pad[2];
  *            uint16 g_begin, g_end; uint8 pad[4].
  * counts[0..3] = number of passes, groups, LUT entries, register blocks.
  * Output arrays may be NULL (sizes only); otherwise they must hold counts[]

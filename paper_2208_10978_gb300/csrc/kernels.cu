@@ -339,6 +339,20 @@ __device__ __forceinline__ void coset_pairs_sw(int a, typename Vec2<R>::type (&v
   }
 }
 
+// Groups K..D-1 of a canonical block: group k pairs along basis bit k and is REAL.
+template <typename R, int D, int K, typename E>
+__device__ __forceinline__ void sweep_canon(typename Vec2<R>::type (&v)[1 << D], const Stage<R, E> &s, int gb,
+                                            uint32_t lane, uint32_t warp, int j) {
+  if constexpr (K < D) {
+    const GroupDesc &g = s.gs[gb + K];
+    const uint32_t cb = s.tcode[gb + K] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
+    const uint4 b4 = *reinterpret_cast<const uint4 *>(g.bccode);
+    const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
+    coset_pairs<R, D, 1 << K, true, E>(v, bw, s.lut + g.lut, cb);
+    sweep_canon<R, D, K + 1, E>(v, s, gb, lane, warp, j);
+  }
+}
+
 // One register block of the sweep.  J cosets per thread (GUARD: at most one).
 template <typename R, int D, int J, bool GUARD>
 __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const BlockDesc &B,
@@ -358,8 +372,13 @@ __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const 
     C2 v[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
+    int g0 = gb;
+    if (!GUARD && B.canon == D) {
+      sweep_canon<R, D, 0, E>(v, s, gb, lane, warp, j);
+      g0 = gb + D;
+    }
 #pragma unroll 1
-    for (int gi = gb; gi < ge; ++gi) {
+    for (int gi = g0; gi < ge; ++gi) {
       const GroupDesc &g = s.gs[gi];
       const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
       const E *L = s.lut + g.lut;
@@ -506,6 +525,21 @@ __device__ __forceinline__ void chunk_expect(int a, const typename Vec2<R>::type
   }
 }
 
+// Groups K..D-1 of a canonical block: group k pairs along basis bit k, Q = 0.
+template <typename R, int D, int JC, int K>
+__device__ __forceinline__ void expect_canon(const typename Vec2<R>::type (&v)[JC][1 << D], R (&e)[JC],
+                                             const Stage<R> &s, int gb, uint32_t lane, uint32_t warp, int j0) {
+  if constexpr (K < D) {
+    const GroupDesc &g = s.gs[gb + K];
+    const uint32_t cb = s.tcode[gb + K] ^ g.blane[lane] ^ g.bwarp[warp];
+    const uint2 b2 = *reinterpret_cast<const uint2 *>(g.bccode);
+#pragma unroll
+    for (int j = 0; j < JC; ++j)
+      e[j] += 2 * coset_expect<R, D, 1 << K, true>(v[j], b2, s.lut + g.lut, cb ^ g.bjcode[j0 + j]);
+    expect_canon<R, D, JC, K + 1>(v, e, s, gb, lane, warp, j0);
+  }
+}
+
 // One register block of the expectation.  The thread's J cosets are taken in
 // chunks of JC (JC * 2^D amplitudes in registers); for each chunk it walks the
 // block's groups once.  Each coset's contribution is summed over the groups in
@@ -535,8 +569,13 @@ __device__ __forceinline__ void expect_block(const typename Vec2<R>::type *tile,
     R e[JC];
 #pragma unroll
     for (int j = 0; j < JC; ++j) e[j] = 0;
+    int g0 = gb;
+    if (!GUARD && B.canon == D) {
+      expect_canon<R, D, JC, 0>(v, e, s, gb, lane, warp, j0);
+      g0 = gb + D;
+    }
 #pragma unroll 1
-    for (int gi = gb; gi < ge; ++gi) {
+    for (int gi = g0; gi < ge; ++gi) {
       const GroupDesc &g = s.gs[gi];
       const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp];
       const C2 *L = s.lut + g.lut;
@@ -578,7 +617,7 @@ __device__ __forceinline__ void expect_block_any(const typename Vec2<R>::type *t
 }
 
 template <typename R, bool STREAM, int TT, bool GUARD>
-__global__ void __launch_bounds__(NT, 2) k_expect(const R *psi, int n, PassDesc pd,
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *psi, int n, PassDesc pd,
                                                   const GroupDesc *groups, const BlockDesc *blocks,
                                                   const typename Vec2<R>::type *lut, double *partial,
                                                   int first_pass) {

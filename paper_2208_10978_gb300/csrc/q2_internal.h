@@ -95,7 +95,9 @@ struct alignas(16) BlockDesc {
   uint16_t uj[16];         // local offset of coset j for thread 0: base(NT * j)
   uint8_t d;               // span dimension, 1..D_MAX
   uint8_t piv[D_MAX];      // pivots, ascending
-  uint8_t pad0[3];
+  uint8_t canon;           // number of leading groups k = 0..canon-1 with a = 1 << k and real
+                           // pair coefficients (REAL kind), unrolled with fixed pair offsets
+  uint8_t pad0[2];
   uint16_t g_begin, g_end; // groups of the block, relative to the pass
   uint8_t pad1[4];
 };

@@ -250,10 +250,12 @@ void form_blocks(std::vector<GroupDesc> &groups, size_t first, size_t last, int 
     for (int64_t j = 0; j < J; ++j) b.uj[j] = (uint16_t)block_base((uint32_t)(NT * j), b);
     b.g_begin = (uint16_t)(g - first);
     b.g_end = (uint16_t)(e - first);
-    for (size_t k = g; k < e; ++k) {
-      GroupDesc &d = groups[k];
+    for (size_t kk = g; kk < e; ++kk) {
+      GroupDesc &d = groups[kk];
       // coordinates of xl in the basis v
       d.a = d.xl ? (uint8_t)span.coords(d.xl) : (uint8_t)0;
+      const int k = (int)(kk - g);
+      if (k == b.canon && k < b.d && d.kind == KIND_REAL && d.a == (1u << k)) ++b.canon;
       for (uint32_t c = 0; c < (1u << b.d); ++c) d.bccode[c] = (uint8_t)local_code(d, b.comb[c], T);
       for (int64_t j = 0; j < J; ++j) d.bjcode[j] = (uint8_t)local_code(d, b.uj[j], T);
       for (int lane = 0; lane < 32; ++lane) d.blane[lane] = (uint8_t)local_code(d, block_base(lane, b), T);

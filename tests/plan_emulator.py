@@ -28,7 +28,7 @@ GROUP_DT = np.dtype([("bp", "<u8", 8), ("xl", "<u4"), ("lut", "<u4"), ("rot0", "
                      ("blane", "u1", 32), ("bwarp", "u1", 8), ("pivot", "u1"), ("pad0", "u1", 7),
                      ("pjcode", "u1", 32), ("plane", "u1", 32), ("pwarp", "u1", 8), ("pu", "<u2", 16),
                      ("pad1", "u1", 8)])
-BLOCK_DT = np.dtype([("comb", "<u2", 16), ("uj", "<u2", 16), ("d", "u1"), ("piv", "u1", 4), ("pad0", "u1", 3),
+BLOCK_DT = np.dtype([("comb", "<u2", 16), ("uj", "<u2", 16), ("d", "u1"), ("piv", "u1", 4), ("canon", "u1"), ("pad0", "u1", 2),
                      ("g_begin", "<u2"), ("g_end", "<u2"), ("pad1", "u1", 4)])
 assert PASS_DT.itemsize == 152 and GROUP_DT.itemsize == 272 and BLOCK_DT.itemsize == 80
 
