@@ -64,8 +64,15 @@ struct SmemLayout {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
+// lut_align: alignment of the staged LUT (bytes, a power of two).  Kernels
+// that address a group's LUT by XOR (byte offset | code << log2(entry)) need
+// it to be entry bytes << (max code bits); groups start at multiples of 2^r
+// entries, so the offset of every group's table then has r free low bits.
+__host__ __device__ inline size_t align_to(size_t v, size_t a) { return (v + a - 1) & ~(a - 1); }
+
 __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc &pd, int vectors,
-                                                  size_t extra_bytes, int lut_entry_bytes = 0) {
+                                                  size_t extra_bytes, int lut_entry_bytes = 0,
+                                                  size_t lut_align = 16) {
   if (lut_entry_bytes == 0) lut_entry_bytes = amp_bytes;
   SmemLayout L;
   size_t o = 0;
@@ -77,6 +84,7 @@ __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc 
   o = align16(o + sizeof(GroupDesc) * (size_t)(pd.g_end - pd.g_begin));
   L.blocks = o;
   o = align16(o + sizeof(BlockDesc) * (size_t)(pd.b_end - pd.b_begin));
+  o = align_to(o, lut_align);
   L.lut = o;
   o = align16(o + (size_t)lut_entry_bytes * (size_t)pd.lut_count);
   L.tcode = o;
@@ -113,6 +121,7 @@ template <typename R, typename E = typename Vec2<R>::type> struct Stage {
   const BlockDesc *bs;   // staged blocks of the pass (index b - b_begin)
   const E *lut;          // staged LUT, indexed by the global LUT offset
   uint32_t *tcode;       // per-tile code of each group
+  const unsigned char *base;   // start of the dynamic shared memory (tile at offset 0)
 };
 
 template <typename T>
@@ -153,6 +162,7 @@ __device__ __forceinline__ Stage<R, E> stage_pass(unsigned char *smem, const Pas
   t.gs = reinterpret_cast<const GroupDesc *>(smem + L.groups);
   t.bs = reinterpret_cast<const BlockDesc *>(smem + L.blocks);
   t.lut = ld - pd.lut_begin;
+  t.base = smem;
   t.tcode = reinterpret_cast<uint32_t *>(smem + L.tcode);
   return t;
 }
@@ -339,16 +349,52 @@ __device__ __forceinline__ void coset_pairs_sw(int a, typename Vec2<R>::type (&v
   }
 }
 
+__host__ __device__ constexpr int log2_int(unsigned v) { return v <= 1 ? 0 : 1 + log2_int(v >> 1); }
+
+// Byte offsets of the 2^D combos of a coset, built by one XOR each:
+// off(c) = off(c without its top bit) ^ W[top bit].
+template <int D>
+__device__ __forceinline__ uint32_t combo_off(uint32_t o0, const uint32_t (&W)[D], int c) {
+  uint32_t o = o0;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+    if ((c >> i) & 1) o ^= W[i];
+  return o;
+}
+
+// Byte offsets (from the start of shared memory) of a canonical group's LUT
+// entries for the combos of one coset: the group's table starts at a
+// multiple of 2^r entries, so entry (cb ^ code) sits at goff | (cb ^ code) << ES
+// and XOR walks from one combo's entry to the next.
+template <int D, int ES>
+__device__ __forceinline__ void group_gens(const GroupDesc &g, int skip, uint32_t (&G)[D]) {
+  const uint4 b4 = *reinterpret_cast<const uint4 *>(g.bccode);
+  const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const int c = 1 << i;
+    G[i] = i == skip ? 0u : (((bw[c >> 2] >> (8 * (c & 3))) & 0xffu) << ES);
+  }
+}
+
 // Groups K..D-1 of a canonical block: group k pairs along basis bit k and is REAL.
 template <typename R, int D, int K, typename E>
 __device__ __forceinline__ void sweep_canon(typename Vec2<R>::type (&v)[1 << D], const Stage<R, E> &s, int gb,
                                             uint32_t lane, uint32_t warp, int j) {
   if constexpr (K < D) {
+    constexpr int ES = log2_int(sizeof(E));
     const GroupDesc &g = s.gs[gb + K];
     const uint32_t cb = s.tcode[gb + K] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
-    const uint4 b4 = *reinterpret_cast<const uint4 *>(g.bccode);
-    const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
-    coset_pairs<R, D, 1 << K, true, E>(v, bw, s.lut + g.lut, cb);
+    const uint32_t goff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + g.lut) - s.base);
+    const uint32_t lp = goff | (cb << ES);
+    uint32_t G[D];
+    group_gens<D, ES>(g, K, G);
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+      if ((c >> K) & 1) continue;
+      const E cs = *reinterpret_cast<const E *>(s.base + combo_off<D>(lp, G, c));
+      rot_real(v[c], v[c | (1 << K)], cs);
+    }
     sweep_canon<R, D, K + 1, E>(v, s, gb, lane, warp, j);
   }
 }
@@ -366,12 +412,17 @@ __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const 
 #pragma unroll
   for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
   const int gb = B.g_begin, ge = B.g_end;
+  constexpr int CS = log2_int(sizeof(C2));
+  unsigned char *tb = reinterpret_cast<unsigned char *>(tile);
+  uint32_t W[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) W[i] = (uint32_t)B.comb[1 << i] << CS;
 #pragma unroll 1
   for (int j = 0; j < J; ++j) {
-    const uint32_t bj = bt ^ B.uj[j];
+    const uint32_t o0 = (bt ^ B.uj[j]) << CS;
     C2 v[N];
 #pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = tile[bj ^ B.comb[c]];
+    for (int c = 0; c < N; ++c) v[c] = *reinterpret_cast<const C2 *>(tb + combo_off<D>(o0, W, c));
     int g0 = gb;
     if (!GUARD && B.canon == D) {
       sweep_canon<R, D, 0, E>(v, s, gb, lane, warp, j);
@@ -398,7 +449,7 @@ __device__ __forceinline__ void sweep_block(typename Vec2<R>::type *tile, const 
       }
     }
 #pragma unroll
-    for (int c = 0; c < N; ++c) tile[bj ^ B.comb[c]] = v[c];
+    for (int c = 0; c < N; ++c) *reinterpret_cast<C2 *>(tb + combo_off<D>(o0, W, c)) = v[c];
   }
 }
 
@@ -433,7 +484,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   using E = typename SweepLut<R>::E;
-  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, 0, sizeof(E));
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, 0, sizeof(E), sizeof(E) << R_MAX_ROT);
   const Stage<R, E> st = stage_pass<R, E>(smem, pd, L, groups, blocks, lut);
   C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   __syncthreads();
@@ -530,12 +581,26 @@ template <typename R, int D, int JC, int K>
 __device__ __forceinline__ void expect_canon(const typename Vec2<R>::type (&v)[JC][1 << D], R (&e)[JC],
                                              const Stage<R> &s, int gb, uint32_t lane, uint32_t warp, int j0) {
   if constexpr (K < D) {
+    using C2 = typename Vec2<R>::type;
+    constexpr int ES = log2_int(sizeof(C2));
     const GroupDesc &g = s.gs[gb + K];
     const uint32_t cb = s.tcode[gb + K] ^ g.blane[lane] ^ g.bwarp[warp];
-    const uint2 b2 = *reinterpret_cast<const uint2 *>(g.bccode);
+    const uint32_t goff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + g.lut) - s.base);
+    uint32_t G[D];
+    group_gens<D, ES>(g, K, G);
 #pragma unroll
-    for (int j = 0; j < JC; ++j)
-      e[j] += 2 * coset_expect<R, D, 1 << K, true>(v[j], b2, s.lut + g.lut, cb ^ g.bjcode[j0 + j]);
+    for (int j = 0; j < JC; ++j) {
+      const uint32_t lp = goff | ((cb ^ g.bjcode[j0 + j]) << ES);
+      R t = 0;
+#pragma unroll
+      for (int c = 0; c < (1 << D); ++c) {
+        if ((c >> K) & 1) continue;
+        const R r = *reinterpret_cast<const R *>(s.base + combo_off<D>(lp, G, c));
+        const C2 a = v[j][c], b = v[j][c | (1 << K)];
+        t += r * (a.x * b.x + a.y * b.y);
+      }
+      e[j] += 2 * t;
+    }
     expect_canon<R, D, JC, K + 1>(v, e, s, gb, lane, warp, j0);
   }
 }
@@ -557,14 +622,19 @@ __device__ __forceinline__ void expect_block(const typename Vec2<R>::type *tile,
 #pragma unroll
   for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
   const int gb = B.g_begin, ge = B.g_end;
+  constexpr int CS = log2_int(sizeof(C2));
+  const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile);
+  uint32_t W[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) W[i] = (uint32_t)B.comb[1 << i] << CS;
 #pragma unroll 1
   for (int j0 = 0; j0 < J; j0 += JC) {
     C2 v[JC][N];
 #pragma unroll
     for (int j = 0; j < JC; ++j) {
-      const uint32_t bj = bt ^ B.uj[j0 + j];
+      const uint32_t o0 = (bt ^ B.uj[j0 + j]) << CS;
 #pragma unroll
-      for (int c = 0; c < N; ++c) v[j][c] = tile[bj ^ B.comb[c]];
+      for (int c = 0; c < N; ++c) v[j][c] = *reinterpret_cast<const C2 *>(tb + combo_off<D>(o0, W, c));
     }
     R e[JC];
 #pragma unroll
@@ -624,7 +694,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32));
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 1, sizeof(double) * (NT / 32), sizeof(C2), sizeof(C2) << R_MAX);
   const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
   C2 *tile = reinterpret_cast<C2 *>(smem + L.tiles);
   double *red = reinterpret_cast<double *>(smem + L.extra);
@@ -957,7 +1027,8 @@ int blocks_per_sm(K kernel, size_t smem) {
 // (tile size T, smallest chunk, fullest staged tables).  The attribute is
 // per-function state shared by every host thread, so it is always set to this
 // fixed value, never to one launch's size.
-size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry_bytes = 0) {
+size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry_bytes = 0,
+                  size_t lut_align = 16) {
   if (lut_entry_bytes == 0) lut_entry_bytes = amp_bytes;
   PassDesc pd{};
   pd.T = T <= 8 ? 8 : T;
@@ -973,6 +1044,7 @@ size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry
   o = align16(o + sizeof(uint64_t) * ((size_t)1 << (pd.T - pd.C)));
   o = align16(o + sizeof(GroupDesc) * G_STAGE);
   o = align16(o + sizeof(BlockDesc) * G_STAGE);
+  o = align_to(o, lut_align);
   o = align16(o + (size_t)lut_entry_bytes * LUT_STAGE);
   o = align16(o + sizeof(uint32_t) * G_STAGE);
   o = align16(o + extra);
@@ -1023,7 +1095,9 @@ PassDesc worst_pass(int T, int C) {
 }  // namespace
 
 size_t tile_smem_bytes(int amp_bytes, int T, int C, int vectors) {
-  return smem_layout(amp_bytes, worst_pass(T, C), vectors, sizeof(double) * (NT / 32)).total;
+  return smem_layout(amp_bytes, worst_pass(T, C), vectors, sizeof(double) * (NT / 32), amp_bytes,
+                     (size_t)amp_bytes << R_MAX)
+      .total;
 }
 
 size_t reverse_smem_bytes(int amp_bytes, int T, int C) {
@@ -1056,9 +1130,9 @@ cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *gro
   using C2 = typename Vec2<R>::type;
   const int nvec = 1;
   const int eb = (int)sizeof(typename SweepLut<R>::E);
-  const size_t smem = smem_layout(sizeof(C2), pd, nvec, 0, eb).total;
+  const size_t smem = smem_layout(sizeof(C2), pd, nvec, 0, eb, (size_t)eb << R_MAX_ROT).total;
   auto k = Q2_DISPATCH(k_sweep, R, n, pd.T);
-  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, 0, eb));
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, 0, eb, (size_t)eb << R_MAX_ROT));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
   k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut));
@@ -1071,7 +1145,7 @@ int expect_grid(int n, int T, int C) {
   const int nvec = 1;
   const size_t smem = tile_smem_bytes(sizeof(C2), T, C, nvec);
   auto k = Q2_DISPATCH(k_expect, R, n, T);
-  prepare(k, worst_smem(sizeof(C2), T, nvec, sizeof(double) * (NT / 32)));
+  prepare(k, worst_smem(sizeof(C2), T, nvec, sizeof(double) * (NT / 32), sizeof(C2), sizeof(C2) << R_MAX));
   return (int)grid_for(1ull << (n - T), blocks_per_sm(k, smem));
 }
 
@@ -1081,9 +1155,11 @@ cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDe
                           cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const int nvec = 1;
-  const size_t smem = smem_layout(sizeof(C2), pd, nvec, sizeof(double) * (NT / 32)).total;
+  const size_t smem =
+      smem_layout(sizeof(C2), pd, nvec, sizeof(double) * (NT / 32), sizeof(C2), sizeof(C2) << R_MAX).total;
   auto k = Q2_DISPATCH(k_expect, R, n, pd.T);
-  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, sizeof(double) * (NT / 32)));
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, sizeof(double) * (NT / 32), sizeof(C2),
+                                        sizeof(C2) << R_MAX));
   if (e != cudaSuccess) return e;
   k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), partial,
                             first ? 1 : 0);

@@ -81,6 +81,8 @@ struct RawGroup {
   Gf2Basis basis;                 // span of the members' zmasks
 };
 
+int align_up_int(int v, int a) { return (v + a - 1) / a * a; }
+
 uint64_t nmask_of(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
 
 // Local basis of a pass: e_0..e_{C-1} first (C as large as the span allows),
@@ -332,8 +334,9 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
       const uint64_t xg = groups[g].x;
       const int m = (int)groups[g].members.size();
       const int nl = 1 << groups[g].basis.rank();
+      const int lut_at = align_up_int(luts, nl);   // every group's table starts at a multiple of 2^r
       const bool fits = (xg == 0 || W.contains(xg) || W.rank() < T) && rots + m <= RP_MAX &&
-                        (int)(g - cur.gb) < G_STAGE && luts + nl <= LUT_STAGE;
+                        (int)(g - cur.gb) < G_STAGE && lut_at + nl <= LUT_STAGE;
       if (!fits && g > cur.gb) {
         cur.ge = g;
         ranges.push_back(cur);
@@ -345,7 +348,7 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
       }
       if (xg != 0 && W.add(xg)) cur.gens.push_back(xg);
       rots += m;
-      luts += nl;
+      luts = align_up_int(luts, nl) + nl;
     }
     if (cur.gb < groups.size()) {
       cur.ge = groups.size();
@@ -363,8 +366,10 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
     PassDesc pd = make_pass(tl);
     pd.g_begin = (int)P.groups.size();
     pd.rot_begin = (int)groups[pr.gb].members.front();
+    lut = (uint32_t)align_up_int((int)lut, 1 << R_MAX_ROT);
     for (size_t g = pr.gb; g < pr.ge; ++g) {
       const RawGroup &rg = groups[g];
+      lut = (uint32_t)align_up_int((int)lut, 1 << rg.basis.rank());
       GroupDesc d = make_desc(rg, tl, lut);
       d.m = (uint8_t)rg.members.size();
       d.rot0 = (uint32_t)(rg.members.front() - pd.rot_begin);
@@ -475,7 +480,7 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       if (popc64(groups[g].x | lowmask) <= T) continue;
       const int nl = 1 << groups[g].basis.rank();
       if ((!W.contains(groups[g].x) && W.rank() >= T) || (int)cur.size() >= G_STAGE ||
-          luts + nl > LUT_STAGE) {
+          align_up_int(luts, nl) + nl > LUT_STAGE) {
         luts = 0;
         pass_groups.push_back(cur);
         pass_gens.push_back(gens);
@@ -483,7 +488,7 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       }
       if (W.add(groups[g].x)) gens.push_back(groups[g].x);
       cur.push_back(g);
-      luts += nl;
+      luts = align_up_int(luts, nl) + nl;
       done[g] = 1;
       --remaining;
     }
@@ -503,14 +508,14 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       for (size_t g = 0; g < groups.size() && !full; ++g)
         if (!done[g] && (groups[g].x & ~L) == 0) {
           const int nl = 1 << groups[g].basis.rank();
-          if ((int)chosen.size() >= G_STAGE || luts + nl > LUT_STAGE) {
+          if ((int)chosen.size() >= G_STAGE || align_up_int(luts, nl) + nl > LUT_STAGE) {
             full = true;
             break;
           }
           done[g] = 1;
           --remaining;
           chosen.push_back(g);
-          luts += nl;
+          luts = align_up_int(luts, nl) + nl;
         }
       if (remaining == 0 || full) break;
       int freq[64] = {0};
@@ -563,8 +568,10 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
     PassDesc pd = make_pass(tl);
     pd.g_begin = (int)H.groups.size();
     pd.rot_begin = pd.rot_end = 0;
+    lut = (uint32_t)align_up_int((int)lut, 1 << R_MAX);
     for (size_t g : pass_groups[p]) {
       const RawGroup &rg = groups[g];
+      lut = (uint32_t)align_up_int((int)lut, 1 << rg.basis.rank());
       GroupDesc d = make_desc(rg, tl, lut);
       // Every member with an even Y count gives a real pair coefficient
       // (Q = 0 at every code): such groups run the real-coefficient path.

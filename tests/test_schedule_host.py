@@ -169,6 +169,19 @@ def test_schedule_chemistry_hamiltonian(lib):
     assert abs(e - sv.expectation(psi, w.ham.x, w.ham.z, w.ham.c)) < 1e-11
 
 
+def test_lut_tables_aligned(lib):
+    """Every group's LUT starts at a multiple of its 2^r entries and every pass's
+    LUT at a multiple of the largest table (XOR addressing of the entries)."""
+    w = uccsd_energy(10, 5, seed=2)
+    a = w.ansatz
+    rp, rg, rb, rl, sm = emu.rot_plan(lib, 10, a.x, a.z, a.angles(w.theta), 8, 4)
+    hp, hg, hb, hl = emu.ham_plan(lib, 10, w.ham.x, w.ham.z, w.ham.c, 8, 4)
+    for groups, passes, rmax in ((rg, rp, 6), (hg, hp, 8)):
+        assert np.all(groups["lut"] % (1 << groups["r"].astype(np.int64)) == 0)
+        assert np.all(passes["lut_begin"] % (1 << rmax) == 0)
+        assert np.all(passes["lut_count"] <= 1024)
+
+
 def test_real_coefficient_groups(lib):
     """Groups whose members all have an even Y count are marked real and have Q = 0;
     a group with an odd-Y member keeps the general kind."""
