@@ -36,7 +36,10 @@
  * >= n, a non-finite angle, coefficient or theta, a NULL pointer that is not
  * documented as optional, a misaligned device pointer, or a workspace that
  * is too small.  Q2_ERR_CUDA wraps launch and driver errors, Q2_ERR_OOM a
- * failed device allocation.
+ * failed device allocation.  Q2_ERR_TIMEOUT: a bounded device-side wait for
+ * a tile copy gave up (the kernel stops instead of spinning); the calls that
+ * read results back (q2_expectation, q2_expectation_noalloc,
+ * q2_vqe_energy_grad) report it, and results of such a call are not valid.
  */
 #ifndef Q2_H
 #define Q2_H

@@ -370,8 +370,14 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
     const int grid = expect_grid<R>(n, hp->T, std::min(g_chunk[d], hp->T));
     Q2_CUDA(run_expect<R>(psi, n, *hp, *ht, partial, grid, out, st), "expectation");
     if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[2], st), "event");
+    unsigned waits = 0;
     Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
+    Q2_CUDA(read_wait_timeouts_async(&waits, st), "D2H");
     Q2_CUDA(cudaStreamSynchronize(st), "sync");
+    if (waits) {
+      clear_wait_timeouts(st);
+      return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
+    }
     *energy_out = host_out[0] / host_out[1];
     if (timing) {
       g_timing.counts[1] = (double)hp->passes.size() + 1;
@@ -400,9 +406,15 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
     g_timing.valid = true;
   }
   std::vector<double> g(nrot);
+  unsigned waits = 0;
   Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
   if (nrot) Q2_CUDA(cudaMemcpyAsync(g.data(), gphi, sizeof(double) * nrot, cudaMemcpyDeviceToHost, st), "D2H");
+  Q2_CUDA(read_wait_timeouts_async(&waits, st), "D2H");
   Q2_CUDA(cudaStreamSynchronize(st), "sync");
+  if (waits) {
+    clear_wait_timeouts(st);
+    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
+  }
   *energy_out = host_out[0] / host_out[1];
   for (int p = 0; p < a->n_params; ++p) grad_out[p] = 0.0;
   for (size_t k = 0; k < nrot; ++k) grad_out[a->param[k]] += a->coef[k] * g[k];
@@ -647,10 +659,16 @@ q2_status q2_expectation(const void *psi_dev, int n, q2_dtype dtype, const q2_ha
       dtype == Q2_C64
           ? run_expect<float>(static_cast<const float *>(psi_dev), n, *hp, *ht, tmp, grid, tmp + 2 * grid, st)
           : run_expect<double>(static_cast<const double *>(psi_dev), n, *hp, *ht, tmp, grid, tmp + 2 * grid, st);
+  unsigned waits = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp + 2 * grid, sizeof(host_out), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = read_wait_timeouts_async(&waits, st);
   cudaFreeAsync(tmp, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "expectation");
+  if (waits) {
+    clear_wait_timeouts(st);
+    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
+  }
   *energy_out = host_out[0] / host_out[1];
   if (norm_out) *norm_out = host_out[1];
   return Q2_OK;

@@ -230,6 +230,83 @@ __device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Stage<R
   }
 }
 
+// ------------------------------------------------------------------ bulk tile copies
+//
+// Tiles move between HBM and shared memory as 2^C-amplitude chunks (128 bytes
+// or more, 16-byte aligned at both ends) by the bulk-copy engine: a thread
+// issues one cp.async.bulk per chunk and the CTA waits on an mbarrier that
+// counts the bytes, so a CTA waiting for its tile issues no instructions and
+// the SM's other CTAs compute meanwhile.  Every wait is bounded: a wait that
+// gives up counts itself in g_wait_timeouts (read and cleared by the host),
+// and the CTA stops working on its tiles.
+
+__device__ unsigned int g_wait_timeouts;
+
+constexpr uint32_t WAIT_POLLS = 1u << 22;   // try_wait polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t i = 0; i < WAIT_POLLS; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  atomicAdd(&g_wait_timeouts, 1u);
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Start the bulk load of tile `base` (completion counted on bar).
+template <typename R, typename E>
+__device__ __forceinline__ void bulk_load_tile(const R *src, uint64_t base, const Stage<R, E> &tc,
+                                               typename Vec2<R>::type *tile, uint64_t *bar) {
+  using C2 = typename Vec2<R>::type;
+  const uint32_t nch = 1u << (tc.T - tc.C);
+  const uint32_t bytes = (uint32_t)sizeof(C2) << tc.C;
+  const C2 *g = reinterpret_cast<const C2 *>(src);
+  if (threadIdx.x == 0) mbar_expect_tx(bar, bytes * nch);
+  for (uint32_t h = threadIdx.x; h < nch; h += NT) bulk_g2s(tile + (h << tc.C), g + (base ^ tc.off[h]), bytes, bar);
+}
+
+// Write tile `base` back; the caller has fenced its shared-memory writes and synced.
+template <typename R, typename E>
+__device__ __forceinline__ void bulk_store_tile(R *dst, uint64_t base, const Stage<R, E> &tc,
+                                                const typename Vec2<R>::type *tile) {
+  using C2 = typename Vec2<R>::type;
+  const uint32_t nch = 1u << (tc.T - tc.C);
+  const uint32_t bytes = (uint32_t)sizeof(C2) << tc.C;
+  C2 *g = reinterpret_cast<C2 *>(dst);
+  for (uint32_t h = threadIdx.x; h < nch; h += NT) bulk_s2g(g + (base ^ tc.off[h]), tile + (h << tc.C), bytes);
+  bulk_commit();
+}
+
 // ------------------------------------------------------------------ complex helpers
 
 template <typename C2, typename R>
@@ -490,17 +567,45 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t base = tile_base(t, pd.umask);
-    load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tile));
-    tile_codes(st, ng, t);
-    __syncthreads();
-    for (int b = 0; b < nb; ++b) {
-      sweep_block_any<R, TT, GUARD>(tile, st.bs[b], st);
+  if constexpr (GUARD) {   // tiles below 2^9 amplitudes: plain loads and stores
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const uint64_t base = tile_base(t, pd.umask);
+      load_tile<R, STREAM>(psi, base, st, reinterpret_cast<V *>(tile));
+      tile_codes(st, ng, t);
+      __syncthreads();
+      for (int b = 0; b < nb; ++b) {
+        sweep_block_any<R, TT, GUARD>(tile, st.bs[b], st);
+        __syncthreads();
+      }
+      store_tile<R, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
       __syncthreads();
     }
-    store_tile<R, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
+  } else {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
+    uint32_t parity = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const uint64_t base = tile_base(t, pd.umask);
+      bulk_load_tile(psi, base, st, tile, &bar);
+      tile_codes(st, ng, t);
+      const bool ok = mbar_wait(&bar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+        break;
+      }
+      for (int b = 0; b < nb; ++b) {
+        sweep_block_any<R, TT, GUARD>(tile, st.bs[b], st);
+        __syncthreads();
+      }
+      fence_proxy_async();   // this thread's tile writes -> visible to the bulk store
+      __syncthreads();
+      bulk_store_tile(psi, base, st, tile);
+      bulk_wait_read();      // the tile may be overwritten once every store has read it
+      __syncthreads();
+    }
+    bulk_wait_all();
   }
 }
 
@@ -702,10 +807,25 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *
   const uint64_t ntiles = 1ull << (n - pd.T);
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   Kahan<R> acc_e, acc_n;
+  __shared__ uint64_t bar;
+  if (!GUARD && threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t parity = 0;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    load_tile<R, STREAM>(psi, tile_base(t, pd.umask), st, reinterpret_cast<V *>(tile));
-    tile_codes(st, ng, t);
-    __syncthreads();
+    if constexpr (GUARD) {
+      load_tile<R, STREAM>(psi, tile_base(t, pd.umask), st, reinterpret_cast<V *>(tile));
+      tile_codes(st, ng, t);
+      __syncthreads();
+    } else {
+      bulk_load_tile(psi, tile_base(t, pd.umask), st, tile, &bar);
+      tile_codes(st, ng, t);
+      const bool ok = mbar_wait(&bar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+        break;
+      }
+    }
     if (first_pass) {
       R s = 0;
       for (uint32_t l = threadIdx.x; l < st.amps; l += NT) {
@@ -1093,6 +1213,16 @@ PassDesc worst_pass(int T, int C) {
 }
 
 }  // namespace
+
+cudaError_t read_wait_timeouts_async(unsigned *host, cudaStream_t st) {
+  return cudaMemcpyFromSymbolAsync(host, g_wait_timeouts, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);
+}
+
+cudaError_t clear_wait_timeouts(cudaStream_t st) {
+  static const unsigned zero = 0;
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_wait_timeouts, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
+  return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+}
 
 size_t tile_smem_bytes(int amp_bytes, int T, int C, int vectors) {
   return smem_layout(amp_bytes, worst_pass(T, C), vectors, sizeof(double) * (NT / 32), amp_bytes,

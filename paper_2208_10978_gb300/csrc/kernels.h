@@ -11,6 +11,9 @@ size_t tile_smem_bytes(int amp_bytes, int T, int C, int vectors);
 size_t reverse_smem_bytes(int amp_bytes, int T, int C);
 int max_grid_blocks(int amp_bytes, int T);
 cudaError_t launch_reduce_pairs(const double *partial, int nblocks, double *out, cudaStream_t st);
+// Bounded device waits that gave up (bulk tile copies), counted since the last clear.
+cudaError_t read_wait_timeouts_async(unsigned *host, cudaStream_t st);
+cudaError_t clear_wait_timeouts(cudaStream_t st);
 
 template <typename R> cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st);
 template <typename R>

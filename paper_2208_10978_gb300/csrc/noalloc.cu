@@ -120,9 +120,15 @@ extern "C" q2_status q2_expectation_noalloc(const void *psi_dev, int n, q2_dtype
             : run<double>(static_cast<const double *>(psi_dev), n, *hp, groups, blocks, base + o_lut, partial, grid, out,
                           st);
   double host_out[2] = {0.0, 0.0};
+  unsigned waits = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = read_wait_timeouts_async(&waits, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return set_error(Q2_ERR_CUDA, cudaGetErrorString(e));
+  if (waits) {
+    clear_wait_timeouts(st);
+    return set_error(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
+  }
   *energy_out = host_out[0] / host_out[1];
   if (norm_out) *norm_out = host_out[1];
   return Q2_OK;
