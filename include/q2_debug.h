@@ -14,8 +14,9 @@
  *   q2_group (272 bytes): uint64 bp[8] code basis in packed-index space;
  *            uint32 xl, lut, rot0; uint8 kind, r, m, a; uint8 bjcode[16],
  *            bccode[16], blane[32], bwarp[8] (register-block enumeration);
- *            uint8 pivot, pad[7], pjcode[32], plane[32], pwarp[8]; uint16 pu[16]
- *            (pair enumeration); uint8 pad[8].
+ *            uint8 pivot, one_param, pad[2]; uint32 wlut; uint8 pjcode[32],
+ *            plane[32], pwarp[8]; uint16 pu[16] (pair enumeration); uint8 pad[8].
+ *            one_param/wlut are set only for ansatz handles (gradient weights).
  *   q2_block (80 bytes): uint16 comb[16], uj[16]; uint8 d, piv[4], canon, pad[2];
  *            uint16 g_begin, g_end; uint8 pad[4].
  * counts[0..3] = number of passes, groups, LUT entries, register blocks.

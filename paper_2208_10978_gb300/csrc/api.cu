@@ -118,15 +118,18 @@ struct DevTables {
   BlockDesc *blocks = nullptr;
   void *lut = nullptr;          // Hamiltonian LUT in the dtype's precision
   uint64_t *signmask = nullptr; // rotation sign masks
+  void *wlut = nullptr;         // gradient weights of one-parameter rotation groups (dtype precision)
   void release() {
     if (groups) cudaFree(groups);
     if (blocks) cudaFree(blocks);
     if (lut) cudaFree(lut);
     if (signmask) cudaFree(signmask);
+    if (wlut) cudaFree(wlut);
     groups = nullptr;
     blocks = nullptr;
     lut = nullptr;
     signmask = nullptr;
+    wlut = nullptr;
     ready = false;
   }
 };
@@ -228,6 +231,7 @@ q2_status ansatz_tables(const q2_ansatz *ac, q2_dtype d, const RotPlan **plan, c
     try {
       a->plan[d] = build_rot_plan(a->n, (int64_t)a->x.size(), a->x.data(), a->z.data(), tile_bits(d),
                                   g_chunk[d]);
+      set_param_weights(a->plan[d], a->param.data(), a->coef.data());
     } catch (const std::exception &e) {
       return fail(Q2_ERR_INVALID, std::string("rotation schedule: ") + e.what());
     }
@@ -260,6 +264,12 @@ q2_status ansatz_tables(const q2_ansatz *ac, q2_dtype d, const RotPlan **plan, c
     if (!p.signmask.empty())
       Q2_CUDA(cudaMemcpy(t.signmask, p.signmask.data(), sizeof(uint64_t) * p.signmask.size(),
                          cudaMemcpyHostToDevice), "upload sign masks");
+    const std::vector<unsigned char> wb = lut_bytes(p.wlut.empty() ? std::vector<double>(1, 0.0) : p.wlut, d);
+    if (cudaMalloc(&t.wlut, wb.size()) != cudaSuccess) {
+      t.release();
+      return fail(Q2_ERR_OOM, "cudaMalloc(gradient weights)");
+    }
+    Q2_CUDA(cudaMemcpy(t.wlut, wb.data(), wb.size(), cudaMemcpyHostToDevice), "upload gradient weights");
     t.device = device;
     t.T = p.T;
     t.ready = true;
@@ -395,7 +405,7 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[2], st), "event");
   for (size_t i = rp->passes.size(); i-- > 0;) {
     Q2_CUDA(launch_reverse<R>(psi, lam, n, rp->passes[i], rt->groups, base + L.lut, rt->signmask,
-                              partial, gphi, st), "reverse sweep");
+                              static_cast<const R *>(rt->wlut), partial, gphi, st), "reverse sweep");
   }
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[3], st), "event");
   if (timing) {
@@ -417,7 +427,7 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
   }
   *energy_out = host_out[0] / host_out[1];
   for (int p = 0; p < a->n_params; ++p) grad_out[p] = 0.0;
-  for (size_t k = 0; k < nrot; ++k) grad_out[a->param[k]] += a->coef[k] * g[k];
+  for (size_t k = 0; k < nrot; ++k) grad_out[a->param[k]] += rp->fold[k] * g[k];
   return Q2_OK;
 }
 

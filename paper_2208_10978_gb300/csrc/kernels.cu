@@ -997,7 +997,8 @@ template <typename R, bool STREAM, int TT, bool GUARD>
 __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDesc pd,
                                                    const GroupDesc *groups,
                                                    const typename Vec2<R>::type *lut,
-                                                   const uint64_t *signmask, double *partial) {
+                                                   const uint64_t *signmask, const R *wlut,
+                                                   double *partial) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   constexpr int P = PairShape<TT, GUARD>::P;
@@ -1026,7 +1027,12 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
     for (int k = ng - 1; k >= 0; --k) {
       const GroupDesc &d = st.gs[k];
       const C2 *lt = st.lut + d.lut;
-      const int kind = d.kind, m = d.m;
+      const int kind = d.kind;
+      // One-parameter groups accumulate sum_pairs w(code) val, w = sum_k coef_k sign_k(code),
+      // in one slot (credited to the group's first rotation); others one slot per rotation.
+      const bool one = d.one_param != 0;
+      const int m = one ? 1 : d.m;
+      const R *wl = wlut + d.wlut;
       const int rot0 = (int)d.rot0;
       const uint64_t *sm = signmask + pd.rot_begin + rot0;
       const uint32_t code0 = st.tcode[k] ^ d.plane[lane] ^ d.pwarp[warp];
@@ -1034,7 +1040,7 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
       R a_k[M_MAX];
 #pragma unroll
       for (int q = 0; q < M_MAX; ++q) {
-        mask[q] = q < m ? __ldg(&sm[q]) : 0ull;
+        mask[q] = (!one && q < m) ? __ldg(&sm[q]) : 0ull;
         a_k[q] = 0;
       }
       if (kind == KIND_DIAG) {
@@ -1046,9 +1052,13 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
           const C2 cs = lt[code];
           const C2 a = tp[l], b = tl[l];
           const R val = b.x * a.y - b.y * a.x;   // Im(conj(lam) psi)
+          if (one) {
+            a_k[0] += __ldg(wl + code) * val;
+          } else {
 #pragma unroll
-          for (int q = 0; q < M_MAX; ++q)
-            if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
+            for (int q = 0; q < M_MAX; ++q)
+              if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
+          }
           C2 a2 = a, b2 = b;
           phase(a2, cs.x, -cs.y);
           phase(b2, cs.x, -cs.y);
@@ -1072,9 +1082,13 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
             // Im(conj(lam_i) psi_j + conj(lam_j) psi_i)
             val = (la.x * pb.y - la.y * pb.x) + (lb.x * pa.y - lb.y * pa.x);
           }
+          if (one) {
+            a_k[0] += __ldg(wl + code) * val;
+          } else {
 #pragma unroll
-          for (int q = 0; q < M_MAX; ++q)
-            if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
+            for (int q = 0; q < M_MAX; ++q)
+              if (q < m) a_k[q] += ((mask[q] >> code) & 1) ? -val : val;
+          }
           if (kind == KIND_REAL) {
             rot_real(pa, pb, cs.x, -cs.y);
             rot_real(la, lb, cs.x, -cs.y);
@@ -1332,8 +1346,8 @@ cudaError_t launch_dot(const R *psi, const R *lam, int n, double *partial, int g
 
 template <typename R>
 cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
-                           const void *lut, const uint64_t *signmask, double *partial, double *gphi,
-                           cudaStream_t st) {
+                           const void *lut, const uint64_t *signmask, const R *wlut, double *partial,
+                           double *gphi, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   PassDesc pq = pd;
   pq.b_begin = pq.b_end = 0;
@@ -1343,7 +1357,7 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
   cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, sizeof(double) * RP_MAX + sizeof(R) * (NT / 32) * M_MAX));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
-  k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), signmask, partial);
+  k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), signmask, wlut, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nrot = pd.rot_end - pd.rot_begin;
   k_reduce_rot<<<(nrot + 127) / 128, 128, 0, st>>>(partial, (int)grid, nrot, gphi + pd.rot_begin);
@@ -1363,8 +1377,8 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
   template int dot_grid<R>(int);                                                                    \
   template cudaError_t launch_dot<R>(const R *, const R *, int, double *, int, cudaStream_t);       \
   template cudaError_t launch_reverse<R>(R *, R *, int, const PassDesc &, const GroupDesc *,        \
-                                         const void *, const uint64_t *, double *, double *,        \
-                                         cudaStream_t);
+                                         const void *, const uint64_t *, const R *, double *,       \
+                                         double *, cudaStream_t);
 
 Q2_INST(float)
 Q2_INST(double)

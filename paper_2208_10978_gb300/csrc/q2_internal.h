@@ -81,7 +81,10 @@ struct alignas(16) GroupDesc {
   // pair enumeration (H apply, reverse sweep): pair q = tid + NT*j is local
   // index insert_zero(q, pivot), partner ^ xl; diagonal groups use l = tid + NT*j
   uint8_t pivot;           // highest bit of xl
-  uint8_t pad0[7];
+  uint8_t one_param;       // rotation groups: every rotation shares one parameter (reverse sweep
+                           // accumulates dE/dtheta of the group with the weights at wlut)
+  uint8_t pad0[2];
+  uint32_t wlut;           // first entry of the group's gradient weights (2^r entries)
   uint8_t pjcode[32];      // code of the j-th per-thread offset
   uint8_t plane[32];       // code of the lane part of the thread's first element
   uint8_t pwarp[8];        // code of the warp part
@@ -127,6 +130,13 @@ struct RotPlan {
   std::vector<uint64_t> signmask;      // per rotation: bit c set iff its sign at code c is -1
   int64_t lut_entries = 0;
   int max_pass_rots = 0;
+  // Gradient weights of one-parameter groups: w_g(code) = sum_k coef_k sign_k(code)
+  // (set by set_param_weights), and per rotation the factor that folds its
+  // reverse-sweep sum into dE/dtheta: coef_k for rotations of other groups, 1 for
+  // the first rotation of a one-parameter group (its sum already carries the
+  // coefficients) and 0 for the group's other rotations.
+  std::vector<double> wlut;
+  std::vector<double> fold;
   // LUT of (cos b, sin b) for every group and code, b = sum_k sign_k(code) phi_k / 2.
   void build_lut(const double *phi, double *lut2) const;
 };
@@ -143,6 +153,7 @@ struct HamPlan {
 };
 
 RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, int T, int C);
+void set_param_weights(RotPlan &p, const int32_t *param, const double *coef);
 HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z,
                        const double *c, int T, int C);
 int64_t count_x_groups(int64_t n_terms, const uint64_t *x);

@@ -407,6 +407,30 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
   return P;
 }
 
+void set_param_weights(RotPlan &p, const int32_t *param, const double *coef) {
+  const size_t n_rot = p.signmask.size();
+  p.fold.assign(coef, coef + n_rot);
+  p.wlut.clear();
+  for (size_t g = 0; g < p.groups.size(); ++g) {
+    GroupDesc &d = p.groups[g];
+    const int k0 = p.grp_rot_begin[g];
+    bool one = true;
+    for (int k = k0 + 1; k < k0 + d.m; ++k) one = one && param[k] == param[k0];
+    d.one_param = one ? 1 : 0;
+    d.wlut = 0;
+    if (!one) continue;
+    d.wlut = (uint32_t)p.wlut.size();
+    const uint32_t ncode = 1u << d.r;
+    for (uint32_t c = 0; c < ncode; ++c) {
+      double w = 0.0;
+      for (int k = k0; k < k0 + d.m; ++k) w += ((p.signmask[k] >> c) & 1) ? -coef[k] : coef[k];
+      p.wlut.push_back(w);
+    }
+    p.fold[k0] = 1.0;
+    for (int k = k0 + 1; k < k0 + d.m; ++k) p.fold[k] = 0.0;
+  }
+}
+
 void RotPlan::build_lut(const double *phi, double *lut2) const {
   for (size_t g = 0; g < groups.size(); ++g) {
     const GroupDesc &d = groups[g];

@@ -25,7 +25,8 @@ PASS_DT = np.dtype([("w", "<u8", 13), ("umask", "<u8"), ("T", "<i4"), ("C", "<i4
                     ("lut_begin", "<i4"), ("lut_count", "<i4"), ("b_begin", "<i4"), ("b_end", "<i4")])
 GROUP_DT = np.dtype([("bp", "<u8", 8), ("xl", "<u4"), ("lut", "<u4"), ("rot0", "<u4"), ("kind", "u1"),
                      ("r", "u1"), ("m", "u1"), ("a", "u1"), ("bjcode", "u1", 16), ("bccode", "u1", 16),
-                     ("blane", "u1", 32), ("bwarp", "u1", 8), ("pivot", "u1"), ("pad0", "u1", 7),
+                     ("blane", "u1", 32), ("bwarp", "u1", 8), ("pivot", "u1"), ("one_param", "u1"), ("pad0", "u1", 2),
+                     ("wlut", "<u4"),
                      ("pjcode", "u1", 32), ("plane", "u1", 32), ("pwarp", "u1", 8), ("pu", "<u2", 16),
                      ("pad1", "u1", 8)])
 BLOCK_DT = np.dtype([("comb", "<u2", 16), ("uj", "<u2", 16), ("d", "u1"), ("piv", "u1", 4), ("canon", "u1"), ("pad0", "u1", 2),
