@@ -404,8 +404,9 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
   Q2_CUDA(launch_reduce_pairs(partial, dgrid, out, st), "reduce");
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[2], st), "event");
   for (size_t i = rp->passes.size(); i-- > 0;) {
-    Q2_CUDA(launch_reverse<R>(psi, lam, n, rp->passes[i], rt->groups, base + L.lut, rt->signmask,
-                              static_cast<const R *>(rt->wlut), partial, gphi, st), "reverse sweep");
+    Q2_CUDA(launch_reverse<R>(psi, lam, n, rp->passes[i], rt->groups, rt->blocks, rp->pass_one_param[i] != 0,
+                              base + L.lut, rt->signmask, static_cast<const R *>(rt->wlut), partial, gphi, st),
+            "reverse sweep");
   }
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[3], st), "event");
   if (timing) {

@@ -1126,6 +1126,241 @@ __global__ void __launch_bounds__(NT, 2) k_reverse(R *psi, R *lam, int n, PassDe
   for (int k = threadIdx.x; k < nrot; k += NT) partial[(size_t)blockIdx.x * RP_MAX + k] = acc[k];
 }
 
+// ------------------------------------------------------------------ register-blocked reverse sweep
+//
+// Passes whose groups each share one parameter (every UCCSD excitation) run
+// Algorithm 1's reverse loop on the sweep's register blocks: a thread holds
+// one coset of psi and of lambda, walks the block's groups backwards, and for
+// each group adds w(code) * val over its pairs (val the pair's part of
+// Im<lambda|P|psi>, w = sum_k coef_k sign_k(code) the group's gradient
+// weight), then undoes the group on both vectors.  A group's sum is
+// warp-reduced and kept per warp in shared memory across tiles; at the end of
+// the pass the warps are added in fixed order and the sum is credited to the
+// group's first rotation.  complex64 only (two 16-amplitude cosets fit in
+// registers); other passes use k_reverse.  The weights are staged beside the
+// LUT with the same entry indices, so both are addressed by XOR.
+
+// inverse of rot_real: [[c, s], [-s, c]] with e = (c, c, s, s)
+__device__ __forceinline__ void rot_real_inv(float2 &a, float2 &b, float4 e) {
+  const unsigned long long A = f2_pack(a.x, a.y), B = f2_pack(b.x, b.y);
+  const unsigned long long C = f2_pack(e.x, e.y), S = f2_pack(e.z, e.w);
+  const unsigned long long na = f2_fma(S, B, f2_mul(C, A));
+  const unsigned long long nb = f2_sub(f2_mul(C, B), f2_mul(S, A));
+  a = f2_unpack(na);
+  b = f2_unpack(nb);
+}
+
+// Pairs (c, c ^ A) of one group: weighted gradient sum, then the group undone on psi (v) and lambda (u).
+template <int D, int A, int KIND>
+__device__ __forceinline__ float rev_pairs(float2 (&v)[1 << D], float2 (&u)[1 << D], const unsigned char *base,
+                                           uint32_t lp, uint32_t wp, const uint32_t (&G)[D],
+                                           const uint32_t (&Gw)[D]) {
+  constexpr int HB = 31 - __builtin_clz(A);
+  float acc = 0.f;
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    if ((c >> HB) & 1) continue;
+    const float4 e = *reinterpret_cast<const float4 *>(base + combo_off<D>(lp, G, c));
+    const float w = *reinterpret_cast<const float *>(base + combo_off<D>(wp, Gw, c));
+    const float2 pa = v[c], pb = v[c ^ A], la = u[c], lb = u[c ^ A];
+    float val;
+    if (KIND == KIND_REAL) val = (lb.x * pa.x + lb.y * pa.y) - (la.x * pb.x + la.y * pb.y);
+    else val = (la.x * pb.y - la.y * pb.x) + (lb.x * pa.y - lb.y * pa.x);
+    acc += w * val;
+    if (KIND == KIND_REAL) {
+      rot_real_inv(v[c], v[c ^ A], e);
+      rot_real_inv(u[c], u[c ^ A], e);
+    } else {
+      rot_xrot(v[c], v[c ^ A], e.x, -e.z);
+      rot_xrot(u[c], u[c ^ A], e.x, -e.z);
+    }
+  }
+  return acc;
+}
+
+template <int D, int KIND>
+__device__ __forceinline__ float rev_pairs_sw(int a, float2 (&v)[1 << D], float2 (&u)[1 << D],
+                                              const unsigned char *base, uint32_t lp, uint32_t wp,
+                                              const uint32_t (&G)[D], const uint32_t (&Gw)[D]) {
+  switch (a) {
+#define Q2_RC(X) \
+  case X:        \
+    if constexpr (X < (1 << D)) return rev_pairs<D, X, KIND>(v, u, base, lp, wp, G, Gw); \
+    break;
+    Q2_RC(1) Q2_RC(2) Q2_RC(3) Q2_RC(4) Q2_RC(5) Q2_RC(6) Q2_RC(7) Q2_RC(8)
+    Q2_RC(9) Q2_RC(10) Q2_RC(11) Q2_RC(12) Q2_RC(13) Q2_RC(14) Q2_RC(15)
+#undef Q2_RC
+    default: break;
+  }
+  return 0.f;
+}
+
+struct RevStage {
+  uint32_t w_off;   // byte offset (from the start of shared memory) of the staged weights
+  double *wacc;     // [NT/32][G_STAGE] per-warp group sums
+};
+
+template <int D, int J>
+__device__ __forceinline__ void reverse_block(float2 *tp, float2 *tl, const BlockDesc &B,
+                                              const Stage<float, float4> &s, const RevStage &rs, int lut_begin) {
+  constexpr int N = 1 << D;
+  constexpr int ES = log2_int(sizeof(float4));
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t bt = tid;
+#pragma unroll
+  for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
+  const int gb = B.g_begin, ge = B.g_end;
+  unsigned char *pbase = reinterpret_cast<unsigned char *>(tp);
+  unsigned char *lbase = reinterpret_cast<unsigned char *>(tl);
+  uint32_t W[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) W[i] = (uint32_t)B.comb[1 << i] << 3;
+#pragma unroll 1
+  for (int j = 0; j < J; ++j) {
+    const uint32_t o0 = (bt ^ B.uj[j]) << 3;
+    float2 v[N], u[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      v[c] = *reinterpret_cast<const float2 *>(pbase + combo_off<D>(o0, W, c));
+      u[c] = *reinterpret_cast<const float2 *>(lbase + combo_off<D>(o0, W, c));
+    }
+#pragma unroll 1
+    for (int gi = ge - 1; gi >= gb; --gi) {
+      const GroupDesc &g = s.gs[gi];
+      const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
+      const uint32_t rel = g.lut - (uint32_t)lut_begin;   // entry index in the staged LUT and weights
+      const uint32_t goff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + g.lut) - s.base);
+      const uint32_t lp = goff | (cb << ES);
+      const uint32_t wp = (rs.w_off + (rel << 2)) | (cb << 2);
+      uint32_t G[D], Gw[D];
+      group_gens<D, ES>(g, -1, G);
+#pragma unroll
+      for (int i = 0; i < D; ++i) Gw[i] = G[i] >> (ES - 2);
+      float acc;
+      if (g.kind == KIND_REAL) {
+        acc = rev_pairs_sw<D, KIND_REAL>(g.a, v, u, s.base, lp, wp, G, Gw);
+      } else if (g.kind == KIND_XROT) {
+        acc = rev_pairs_sw<D, KIND_XROT>(g.a, v, u, s.base, lp, wp, G, Gw);
+      } else {
+        acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const float4 e = *reinterpret_cast<const float4 *>(s.base + combo_off<D>(lp, G, c));
+          const float w = *reinterpret_cast<const float *>(s.base + combo_off<D>(wp, Gw, c));
+          acc += w * (u[c].x * v[c].y - u[c].y * v[c].x);
+          phase(v[c], e.x, -e.z);
+          phase(u[c], e.x, -e.z);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) rs.wacc[warp * G_STAGE + gi] += (double)acc;
+    }
+    uint32_t W2[D];   // reloaded rather than kept live across the group loop
+#pragma unroll
+    for (int i = 0; i < D; ++i) W2[i] = (uint32_t)B.comb[1 << i] << 3;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      *reinterpret_cast<float2 *>(pbase + combo_off<D>(o0, W2, c)) = v[c];
+      *reinterpret_cast<float2 *>(lbase + combo_off<D>(o0, W2, c)) = u[c];
+    }
+  }
+}
+
+template <int TT>
+__device__ __forceinline__ void reverse_block_any(float2 *tp, float2 *tl, const BlockDesc &B,
+                                                  const Stage<float, float4> &s, const RevStage &rs,
+                                                  int lut_begin) {
+  switch (B.d) {
+    case 1: reverse_block<1, BlockShape<TT, 1>::J>(tp, tl, B, s, rs, lut_begin); break;
+    case 2:
+      if constexpr (TT >= 10) reverse_block<2, BlockShape<TT, 2>::J>(tp, tl, B, s, rs, lut_begin);
+      break;
+    case 3:
+      if constexpr (TT >= 11) reverse_block<3, BlockShape<TT, 3>::J>(tp, tl, B, s, rs, lut_begin);
+      break;
+    case 4:
+      if constexpr (TT >= 12) reverse_block<4, BlockShape<TT, 4>::J>(tp, tl, B, s, rs, lut_begin);
+      break;
+  }
+}
+
+// Extra shared memory of k_reverse_blk after the staged tables: weights (one
+// float per LUT entry, 256-byte aligned) and the per-warp group sums.
+__host__ __device__ inline size_t rev_extra_bytes(int lut_count) {
+  return 256 + align16(sizeof(float) * (size_t)lut_count) + sizeof(double) * (NT / 32) * G_STAGE;
+}
+
+template <int TT>
+__global__ void __launch_bounds__(NT, 2) k_reverse_blk(float *psi, float *lam, int n, PassDesc pd,
+                                                       const GroupDesc *groups, const BlockDesc *blocks,
+                                                       const float2 *lut, const float *wlut, double *partial) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemLayout L = smem_layout(sizeof(float2), pd, 2, rev_extra_bytes(pd.lut_count), sizeof(float4),
+                                   sizeof(float4) << R_MAX_ROT);
+  const Stage<float, float4> st = stage_pass<float, float4>(smem, pd, L, groups, blocks, lut);
+  float2 *tp = reinterpret_cast<float2 *>(smem + L.tiles);
+  float2 *tl = tp + st.amps;
+  const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
+  RevStage rs;
+  rs.w_off = (uint32_t)((L.extra + 255) & ~(size_t)255);
+  float *wst = reinterpret_cast<float *>(smem + rs.w_off);
+  rs.wacc = reinterpret_cast<double *>(smem + rs.w_off + align16(sizeof(float) * (size_t)pd.lut_count));
+  for (int i = threadIdx.x; i < (NT / 32) * G_STAGE; i += NT) rs.wacc[i] = 0.0;
+  for (int g = threadIdx.x; g < ng; g += NT) {   // weights beside the LUT entries of each group
+    const GroupDesc &d = st.gs[g];
+    const uint32_t rel = d.lut - (uint32_t)pd.lut_begin;
+    for (int c = 0; c < (1 << d.r); ++c) wst[rel + c] = __ldg(wlut + d.wlut + c);
+  }
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pd.T);
+  uint32_t parity = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t base = tile_base(t, pd.umask);
+    const uint32_t nch = 1u << (pd.T - pd.C);
+    const uint32_t bytes = (uint32_t)sizeof(float2) << pd.C;
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 2 * bytes * nch);
+    for (uint32_t h = threadIdx.x; h < nch; h += NT) {
+      const uint64_t gi = base ^ st.off[h];
+      bulk_g2s(tp + (h << pd.C), reinterpret_cast<const float2 *>(psi) + gi, bytes, &bar);
+      bulk_g2s(tl + (h << pd.C), reinterpret_cast<const float2 *>(lam) + gi, bytes, &bar);
+    }
+    tile_codes(st, ng, t);
+    const bool ok = mbar_wait(&bar, parity);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+      break;
+    }
+    for (int b = nb - 1; b >= 0; --b) {
+      reverse_block_any<TT>(tp, tl, st.bs[b], st, rs, pd.lut_begin);
+      __syncthreads();
+    }
+    fence_proxy_async();
+    __syncthreads();
+    for (uint32_t h = threadIdx.x; h < nch; h += NT) {
+      const uint64_t gi = base ^ st.off[h];
+      bulk_s2g(reinterpret_cast<float2 *>(psi) + gi, tp + (h << pd.C), bytes);
+      bulk_s2g(reinterpret_cast<float2 *>(lam) + gi, tl + (h << pd.C), bytes);
+    }
+    bulk_commit();
+    bulk_wait_read();
+    __syncthreads();
+  }
+  bulk_wait_all();
+  // per-rotation partials of this CTA: group sums at each group's first rotation, zero elsewhere
+  const int nrot = pd.rot_end - pd.rot_begin;
+  for (int k = threadIdx.x; k < nrot; k += NT) partial[(size_t)blockIdx.x * RP_MAX + k] = 0.0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < ng; g += NT) {
+    double sum = 0.0;
+    for (int w = 0; w < NT / 32; ++w) sum += rs.wacc[w * G_STAGE + g];
+    partial[(size_t)blockIdx.x * RP_MAX + st.gs[g].rot0] = sum;
+  }
+}
+
 // g[k] = sum_b partial[b][k], fixed order over b.
 __global__ void k_reduce_rot(const double *partial, int nblocks, int nrot, double *g) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1346,9 +1581,32 @@ cudaError_t launch_dot(const R *psi, const R *lam, int n, double *partial, int g
 
 template <typename R>
 cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
-                           const void *lut, const uint64_t *signmask, const R *wlut, double *partial,
-                           double *gphi, cudaStream_t st) {
+                           const BlockDesc *blocks, bool one_param, const void *lut, const uint64_t *signmask,
+                           const R *wlut, double *partial, double *gphi, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
+  if constexpr (sizeof(R) == 4) {
+    if (one_param && pd.T >= 9 && pd.T <= T_LIMIT) {   // register-blocked path (complex64)
+      const size_t eb = sizeof(float4), al = eb << R_MAX_ROT;
+      const size_t smem = smem_layout(sizeof(float2), pd, 2, rev_extra_bytes(pd.lut_count), (int)eb, al).total;
+      decltype(&k_reverse_blk<9>) k;
+      switch (pd.T) {
+        case 9: k = &k_reverse_blk<9>; break;
+        case 10: k = &k_reverse_blk<10>; break;
+        case 11: k = &k_reverse_blk<11>; break;
+        case 12: k = &k_reverse_blk<12>; break;
+        default: k = &k_reverse_blk<13>; break;
+      }
+      cudaError_t e = prepare(k, worst_smem(sizeof(float2), pd.T, 2, rev_extra_bytes(LUT_STAGE), (int)eb, al));
+      if (e != cudaSuccess) return e;
+      const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
+      k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const float2 *>(lut), wlut,
+                                partial);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      const int nrot = pd.rot_end - pd.rot_begin;
+      k_reduce_rot<<<(nrot + 127) / 128, 128, 0, st>>>(partial, (int)grid, nrot, gphi + pd.rot_begin);
+      return cudaGetLastError();
+    }
+  }
   PassDesc pq = pd;
   pq.b_begin = pq.b_end = 0;
   const size_t smem =
@@ -1377,8 +1635,8 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
   template int dot_grid<R>(int);                                                                    \
   template cudaError_t launch_dot<R>(const R *, const R *, int, double *, int, cudaStream_t);       \
   template cudaError_t launch_reverse<R>(R *, R *, int, const PassDesc &, const GroupDesc *,        \
-                                         const void *, const uint64_t *, const R *, double *,       \
-                                         double *, cudaStream_t);
+                                         const BlockDesc *, bool, const void *, const uint64_t *,   \
+                                         const R *, double *, double *, cudaStream_t);
 
 Q2_INST(float)
 Q2_INST(double)

@@ -32,7 +32,7 @@ template <typename R>
 cudaError_t launch_dot(const R *psi, const R *lam, int n, double *partial, int grid, cudaStream_t st);
 template <typename R>
 cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
-                           const void *lut, const uint64_t *signmask, const R *wlut, double *partial,
-                           double *gphi, cudaStream_t st);
+                           const BlockDesc *blocks, bool one_param, const void *lut, const uint64_t *signmask,
+                           const R *wlut, double *partial, double *gphi, cudaStream_t st);
 
 }  // namespace q2

@@ -137,6 +137,7 @@ struct RotPlan {
   // coefficients) and 0 for the group's other rotations.
   std::vector<double> wlut;
   std::vector<double> fold;
+  std::vector<uint8_t> pass_one_param;   // every group of the pass is a one-parameter group
   // LUT of (cos b, sin b) for every group and code, b = sum_k sign_k(code) phi_k / 2.
   void build_lut(const double *phi, double *lut2) const;
 };

@@ -429,6 +429,10 @@ void set_param_weights(RotPlan &p, const int32_t *param, const double *coef) {
     p.fold[k0] = 1.0;
     for (int k = k0 + 1; k < k0 + d.m; ++k) p.fold[k] = 0.0;
   }
+  p.pass_one_param.assign(p.passes.size(), 1);
+  for (size_t i = 0; i < p.passes.size(); ++i)
+    for (int g = p.passes[i].g_begin; g < p.passes[i].g_end; ++g)
+      if (!p.groups[g].one_param) p.pass_one_param[i] = 0;
 }
 
 void RotPlan::build_lut(const double *phi, double *lut2) const {

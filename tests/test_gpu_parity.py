@@ -154,6 +154,42 @@ def test_vqe_energy_grad_matches_oracle(dtype, n, ne, tile):
     assert np.max(np.abs(g - g_ref)) < (1e-9 if dtype == "complex128" else 1e-4)
 
 
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+@pytest.mark.parametrize("shared", [True, False])
+def test_vqe_gradient_generic_rotations(dtype, shared):
+    """Ansatz of arbitrary Pauli strings (x = 0, even- and odd-Y groups), with
+    runs of equal xmasks sharing one parameter (one-parameter groups: the
+    register-blocked reverse sweep) or each rotation its own parameter."""
+    n, ne = 11, 5
+    rng = np.random.default_rng(17 + shared)
+    k = 90
+    x = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    x[rng.random(k) < 0.1] = 0
+    for i in range(1, k):
+        if rng.random() < 0.6:
+            x[i] = x[i - 1]
+    z = rng.integers(0, 1 << n, size=k).astype(np.uint64)
+    if shared:
+        param = np.cumsum(np.concatenate([[0], (x[1:] != x[:-1]).astype(np.int64)])).astype(np.int32)
+    else:
+        param = np.arange(k, dtype=np.int32)
+    n_params = int(param.max()) + 1
+    coef = rng.choice([-1.0, -0.5, 0.25, 1.0], size=k)
+    ans = q2.Ansatz(n, ne, x, z, param, coef, n_params)
+    w = uccsd_energy(10, 5, seed=4)
+    hx = np.concatenate([w.ham.x, [0, 1 << 10]]).astype(np.uint64)
+    hz = np.concatenate([w.ham.z, [1 << 10, 0]]).astype(np.uint64)
+    hc = np.concatenate([w.ham.c, [0.3, -0.2]])
+    ham = q2.Hamiltonian(n, hx, hz, hc)
+    theta = rng.normal(0, 0.4, size=n_params)
+    e, g, _ = q2.vqe_energy_grad(ans, ham, theta, dtype=dtype, want_grad=True)
+    phi = coef * theta[param]
+    e_ref, gphi = c_oracle.energy_and_gradient(n, ne, x, z, phi, hx, hz, hc)
+    g_ref = sv.fold_to_theta(gphi, param, coef, n_params)
+    assert abs(e - e_ref) < TOL_E[dtype]
+    assert np.max(np.abs(g - g_ref)) < (1e-9 if dtype == "complex128" else 1e-4)
+
+
 def test_autograd_function():
     w = uccsd_energy(8, 4, seed=3)
     ans = q2.Ansatz.from_uccsd(w.ansatz)
