@@ -302,7 +302,7 @@ cudaError_t run_expect(const R *psi, int n, const HamPlan &h, const DevTables &t
 template <typename R>
 cudaError_t run_happly(const R *psi, R *lam, int n, const HamPlan &h, const DevTables &t, cudaStream_t st) {
   for (size_t i = 0; i < h.passes.size(); ++i) {
-    cudaError_t e = launch_happly<R>(psi, lam, n, h.passes[i], t.groups, t.lut, i == 0, st);
+    cudaError_t e = launch_happly<R>(psi, lam, n, h.passes[i], t.groups, t.blocks, t.lut, i == 0, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

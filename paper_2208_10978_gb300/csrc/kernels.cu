@@ -959,6 +959,188 @@ __global__ void __launch_bounds__(NT, 3) k_happly(const R *psi, R *lam, int n, P
   }
 }
 
+// ------------------------------------------------------------------ register-blocked H apply
+//
+// lambda += H_pass psi on the Hamiltonian plan's register blocks: a thread
+// holds a chunk of psi cosets and the matching lambda amplitudes in
+// registers and walks the block's groups once; lambda goes back to the tile
+// after each block.  Tiles move by bulk copies; the first pass starts from
+// lambda = 0 without reading it.
+
+// u[c] += (R - iQ) v[c ^ A], u[c ^ A] += (R + iQ) v[c] over the pairs (c, c ^ A).
+template <typename R, int D, int A, bool QZERO>
+__device__ __forceinline__ void coset_happly(const typename Vec2<R>::type (&v)[1 << D],
+                                             typename Vec2<R>::type (&u)[1 << D], const unsigned char *base,
+                                             uint32_t lp, const uint32_t (&G)[D]) {
+  using C2 = typename Vec2<R>::type;
+  constexpr int HB = 31 - __builtin_clz(A);
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    if ((c >> HB) & 1) continue;
+    const C2 rq = *reinterpret_cast<const C2 *>(base + combo_off<D>(lp, G, c));
+    const C2 a = v[c], b = v[c ^ A];
+    if (QZERO) {
+      u[c].x += rq.x * b.x;
+      u[c].y += rq.x * b.y;
+      u[c ^ A].x += rq.x * a.x;
+      u[c ^ A].y += rq.x * a.y;
+    } else {
+      u[c].x += rq.x * b.x + rq.y * b.y;
+      u[c].y += rq.x * b.y - rq.y * b.x;
+      u[c ^ A].x += rq.x * a.x - rq.y * a.y;
+      u[c ^ A].y += rq.x * a.y + rq.y * a.x;
+    }
+  }
+}
+
+template <typename R, int D, bool QZERO>
+__device__ __forceinline__ void coset_happly_sw(int a, const typename Vec2<R>::type (&v)[1 << D],
+                                                typename Vec2<R>::type (&u)[1 << D], const unsigned char *base,
+                                                uint32_t lp, const uint32_t (&G)[D]) {
+  switch (a) {
+#define Q2_HC(X) \
+  case X:        \
+    if constexpr (X < (1 << D)) coset_happly<R, D, X, QZERO>(v, u, base, lp, G); \
+    break;
+    Q2_HC(1) Q2_HC(2) Q2_HC(3) Q2_HC(4) Q2_HC(5) Q2_HC(6) Q2_HC(7)
+#undef Q2_HC
+    default: break;
+  }
+}
+
+template <typename R, int D, int J>
+__device__ __forceinline__ void happly_block(const typename Vec2<R>::type *tp, typename Vec2<R>::type *tl,
+                                             const BlockDesc &B, const Stage<R> &s) {
+  using C2 = typename Vec2<R>::type;
+  constexpr int N = 1 << D;
+  constexpr int AMPS = 8;
+  constexpr int JC = J < AMPS / N ? J : (AMPS / N > 0 ? AMPS / N : 1);
+  constexpr int CS = log2_int(sizeof(C2));
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t bt = tid;
+#pragma unroll
+  for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
+  const int gb = B.g_begin, ge = B.g_end;
+  const unsigned char *pbase = reinterpret_cast<const unsigned char *>(tp);
+  unsigned char *lbase = reinterpret_cast<unsigned char *>(tl);
+  uint32_t W[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) W[i] = (uint32_t)B.comb[1 << i] << CS;
+#pragma unroll 1
+  for (int j0 = 0; j0 < J; j0 += JC) {
+    C2 v[JC][N], u[JC][N];
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
+      const uint32_t o0 = (bt ^ B.uj[j0 + j]) << CS;
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        v[j][c] = *reinterpret_cast<const C2 *>(pbase + combo_off<D>(o0, W, c));
+        u[j][c] = *reinterpret_cast<const C2 *>(lbase + combo_off<D>(o0, W, c));
+      }
+    }
+#pragma unroll 1
+    for (int gi = gb; gi < ge; ++gi) {
+      const GroupDesc &g = s.gs[gi];
+      const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp];
+      constexpr int ES = log2_int(sizeof(C2));
+      const uint32_t goff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + g.lut) - s.base);
+      uint32_t G[D];
+      group_gens<D, ES>(g, -1, G);
+      if (g.kind == KIND_DIAG) {
+#pragma unroll
+        for (int j = 0; j < JC; ++j) {
+          const uint32_t lp = goff | ((cb ^ g.bjcode[j0 + j]) << ES);
+#pragma unroll
+          for (int c = 0; c < N; ++c) {
+            const R dv = reinterpret_cast<const C2 *>(s.base + combo_off<D>(lp, G, c))->x;
+            u[j][c].x += dv * v[j][c].x;
+            u[j][c].y += dv * v[j][c].y;
+          }
+        }
+      } else {
+        const int a = g.a;
+        const bool qz = g.kind == KIND_REAL;
+#pragma unroll
+        for (int j = 0; j < JC; ++j) {
+          const uint32_t lp = goff | ((cb ^ g.bjcode[j0 + j]) << ES);
+          if (qz) coset_happly_sw<R, D, true>(a, v[j], u[j], s.base, lp, G);
+          else coset_happly_sw<R, D, false>(a, v[j], u[j], s.base, lp, G);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
+      const uint32_t o0 = (bt ^ B.uj[j0 + j]) << CS;
+#pragma unroll
+      for (int c = 0; c < N; ++c) *reinterpret_cast<C2 *>(lbase + combo_off<D>(o0, W, c)) = u[j][c];
+    }
+  }
+}
+
+template <typename R, int TT>
+__device__ __forceinline__ void happly_block_any(const typename Vec2<R>::type *tp, typename Vec2<R>::type *tl,
+                                                 const BlockDesc &B, const Stage<R> &s) {
+  switch (B.d) {
+    case 1: happly_block<R, 1, BlockShape<TT, 1>::J>(tp, tl, B, s); break;
+    case 2:
+      if constexpr (TT >= 10) happly_block<R, 2, BlockShape<TT, 2>::J>(tp, tl, B, s);
+      break;
+    case 3:
+      if constexpr (TT >= 11) happly_block<R, 3, BlockShape<TT, 3>::J>(tp, tl, B, s);
+      break;
+  }
+}
+
+template <typename R, int TT>
+__global__ void __launch_bounds__(NT, 2) k_happly_blk(const R *psi, R *lam, int n, PassDesc pd,
+                                                      const GroupDesc *groups, const BlockDesc *blocks,
+                                                      const typename Vec2<R>::type *lut, int first_pass) {
+  using C2 = typename Vec2<R>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemLayout L = smem_layout(sizeof(C2), pd, 2, 0, sizeof(C2), sizeof(C2) << R_MAX);
+  const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
+  C2 *tp = reinterpret_cast<C2 *>(smem + L.tiles);
+  C2 *tl = tp + st.amps;
+  const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pd.T);
+  const uint32_t nch = 1u << (pd.T - pd.C);
+  const uint32_t bytes = (uint32_t)sizeof(C2) << pd.C;
+  uint32_t parity = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t base = tile_base(t, pd.umask);
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, (first_pass ? 1u : 2u) * bytes * nch);
+    for (uint32_t h = threadIdx.x; h < nch; h += NT) {
+      const uint64_t gi = base ^ st.off[h];
+      bulk_g2s(tp + (h << pd.C), reinterpret_cast<const C2 *>(psi) + gi, bytes, &bar);
+      if (!first_pass) bulk_g2s(tl + (h << pd.C), reinterpret_cast<const C2 *>(lam) + gi, bytes, &bar);
+    }
+    if (first_pass)
+      for (uint32_t l = threadIdx.x; l < st.amps; l += NT) tl[l] = C2{0, 0};
+    tile_codes(st, ng, t);
+    const bool ok = mbar_wait(&bar, parity);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+      break;
+    }
+    for (int b = 0; b < nb; ++b) {
+      happly_block_any<R, TT>(tp, tl, st.bs[b], st);
+      __syncthreads();
+    }
+    fence_proxy_async();
+    __syncthreads();
+    for (uint32_t h = threadIdx.x; h < nch; h += NT)
+      bulk_s2g(reinterpret_cast<C2 *>(lam) + (base ^ st.off[h]), tl + (h << pd.C), bytes);
+    bulk_commit();
+    bulk_wait_read();
+    __syncthreads();
+  }
+  bulk_wait_all();
+}
+
 // Re<psi|lam> and <psi|psi>, per-CTA partials.
 template <typename R>
 __global__ void __launch_bounds__(NT) k_dot(const R *psi, const R *lam, uint64_t n_amps,
@@ -1552,8 +1734,25 @@ cudaError_t launch_reduce_pairs(const double *partial, int nblocks, double *out,
 
 template <typename R>
 cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
-                          const void *lut, bool first, cudaStream_t st) {
+                          const BlockDesc *blocks, const void *lut, bool first, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
+  if (blocks && pd.T >= 9 && pd.T <= T_LIMIT) {   // register-blocked path
+    const size_t al = sizeof(C2) << R_MAX;
+    const size_t smem = smem_layout(sizeof(C2), pd, 2, 0, sizeof(C2), al).total;
+    decltype(&k_happly_blk<R, 9>) k;
+    switch (pd.T) {
+      case 9: k = &k_happly_blk<R, 9>; break;
+      case 10: k = &k_happly_blk<R, 10>; break;
+      case 11: k = &k_happly_blk<R, 11>; break;
+      case 12: k = &k_happly_blk<R, 12>; break;
+      default: k = &k_happly_blk<R, 13>; break;
+    }
+    cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0, sizeof(C2), al));
+    if (e != cudaSuccess) return e;
+    const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
+    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), first ? 1 : 0);
+    return cudaGetLastError();
+  }
   PassDesc pq = pd;
   pq.b_begin = pq.b_end = 0;
   const size_t smem = smem_layout(sizeof(C2), pq, 2, 0).total;
@@ -1631,7 +1830,7 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
                                         const BlockDesc *, const void *, double *, int, bool,       \
                                         cudaStream_t);                                              \
   template cudaError_t launch_happly<R>(const R *, R *, int, const PassDesc &, const GroupDesc *,   \
-                                        const void *, bool, cudaStream_t);                          \
+                                        const BlockDesc *, const void *, bool, cudaStream_t);       \
   template int dot_grid<R>(int);                                                                    \
   template cudaError_t launch_dot<R>(const R *, const R *, int, double *, int, cudaStream_t);       \
   template cudaError_t launch_reverse<R>(R *, R *, int, const PassDesc &, const GroupDesc *,        \

@@ -26,7 +26,7 @@ cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDe
                           cudaStream_t st);
 template <typename R>
 cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
-                          const void *lut, bool first, cudaStream_t st);
+                          const BlockDesc *blocks, const void *lut, bool first, cudaStream_t st);
 template <typename R> int dot_grid(int n);
 template <typename R>
 cudaError_t launch_dot(const R *psi, const R *lam, int n, double *partial, int grid, cudaStream_t st);
