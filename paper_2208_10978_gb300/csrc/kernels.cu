@@ -1008,6 +1008,26 @@ __device__ __forceinline__ void coset_happly_sw(int a, const typename Vec2<R>::t
   }
 }
 
+// Groups K..D-1 of a canonical Hamiltonian block: group k pairs along basis bit k, Q = 0.
+template <typename R, int D, int JC, int K>
+__device__ __forceinline__ void happly_canon(const typename Vec2<R>::type (&v)[JC][1 << D],
+                                             typename Vec2<R>::type (&u)[JC][1 << D], const Stage<R> &s, int gb,
+                                             uint32_t lane, uint32_t warp, int j0) {
+  if constexpr (K < D) {
+    using C2 = typename Vec2<R>::type;
+    constexpr int ES = log2_int(sizeof(C2));
+    const GroupDesc &g = s.gs[gb + K];
+    const uint32_t cb = s.tcode[gb + K] ^ g.blane[lane] ^ g.bwarp[warp];
+    const uint32_t goff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + g.lut) - s.base);
+    uint32_t G[D];
+    group_gens<D, ES>(g, K, G);
+#pragma unroll
+    for (int j = 0; j < JC; ++j)
+      coset_happly<R, D, 1 << K, true>(v[j], u[j], s.base, goff | ((cb ^ g.bjcode[j0 + j]) << ES), G);
+    happly_canon<R, D, JC, K + 1>(v, u, s, gb, lane, warp, j0);
+  }
+}
+
 template <typename R, int D, int J>
 __device__ __forceinline__ void happly_block(const typename Vec2<R>::type *tp, typename Vec2<R>::type *tl,
                                              const BlockDesc &B, const Stage<R> &s) {
@@ -1038,8 +1058,13 @@ __device__ __forceinline__ void happly_block(const typename Vec2<R>::type *tp, t
         u[j][c] = *reinterpret_cast<const C2 *>(lbase + combo_off<D>(o0, W, c));
       }
     }
+    int g0 = gb;
+    if (B.canon == D) {
+      happly_canon<R, D, JC, 0>(v, u, s, gb, lane, warp, j0);
+      g0 = gb + D;
+    }
 #pragma unroll 1
-    for (int gi = gb; gi < ge; ++gi) {
+    for (int gi = g0; gi < ge; ++gi) {
       const GroupDesc &g = s.gs[gi];
       const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp];
       constexpr int ES = log2_int(sizeof(C2));
@@ -1382,6 +1407,40 @@ struct RevStage {
   double *wacc;     // [NT/32][G_STAGE] per-warp group sums
 };
 
+// Group k of a canonical block (pairs along basis bit k, REAL): gradient sum and undo.
+template <int D, int K>
+__device__ __forceinline__ float rev_canon_group(float2 (&v)[1 << D], float2 (&u)[1 << D],
+                                                 const Stage<float, float4> &s, const RevStage &rs, int gi,
+                                                 uint32_t cb, int lut_begin) {
+  constexpr int ES = log2_int(sizeof(float4));
+  const GroupDesc &g = s.gs[gi];
+  const uint32_t rel = g.lut - (uint32_t)lut_begin;
+  const uint32_t goff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + g.lut) - s.base);
+  uint32_t G[D], Gw[D];
+  group_gens<D, ES>(g, K, G);
+#pragma unroll
+  for (int i = 0; i < D; ++i) Gw[i] = G[i] >> (ES - 2);
+  return rev_pairs<D, 1 << K, KIND_REAL>(v, u, s.base, goff | (cb << ES), (rs.w_off + (rel << 2)) | (cb << 2), G,
+                                         Gw);
+}
+
+// Canonical groups K, K-1, ..., 0 of a block, in that order (the reverse of the sweep's order).
+template <int D, int K>
+__device__ __forceinline__ void rev_canon(float2 (&v)[1 << D], float2 (&u)[1 << D], const Stage<float, float4> &s,
+                                          const RevStage &rs, int gb, uint32_t lane, uint32_t warp, int j,
+                                          int lut_begin) {
+  if constexpr (K >= 0) {
+    const int gi = gb + K;
+    const GroupDesc &g = s.gs[gi];
+    const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
+    float acc = rev_canon_group<D, K>(v, u, s, rs, gi, cb, lut_begin);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) rs.wacc[warp * G_STAGE + gi] += (double)acc;
+    rev_canon<D, K - 1>(v, u, s, rs, gb, lane, warp, j, lut_begin);
+  }
+}
+
 template <int D, int J>
 __device__ __forceinline__ void reverse_block(float2 *tp, float2 *tl, const BlockDesc &B,
                                               const Stage<float, float4> &s, const RevStage &rs, int lut_begin) {
@@ -1406,8 +1465,10 @@ __device__ __forceinline__ void reverse_block(float2 *tp, float2 *tl, const Bloc
       v[c] = *reinterpret_cast<const float2 *>(pbase + combo_off<D>(o0, W, c));
       u[c] = *reinterpret_cast<const float2 *>(lbase + combo_off<D>(o0, W, c));
     }
+    const bool canon = B.canon == D;
+    const int g_stop = canon ? gb + D : gb;   // canonical leading groups go last, unrolled
 #pragma unroll 1
-    for (int gi = ge - 1; gi >= gb; --gi) {
+    for (int gi = ge - 1; gi >= g_stop; --gi) {
       const GroupDesc &g = s.gs[gi];
       const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp] ^ g.bjcode[j];
       const uint32_t rel = g.lut - (uint32_t)lut_begin;   // entry index in the staged LUT and weights
@@ -1438,6 +1499,7 @@ __device__ __forceinline__ void reverse_block(float2 *tp, float2 *tl, const Bloc
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0) rs.wacc[warp * G_STAGE + gi] += (double)acc;
     }
+    if (canon) rev_canon<D, D - 1>(v, u, s, rs, gb, lane, warp, j, lut_begin);
     uint32_t W2[D];   // reloaded rather than kept live across the group loop
 #pragma unroll
     for (int i = 0; i < D; ++i) W2[i] = (uint32_t)B.comb[1 << i] << 3;
