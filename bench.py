@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the 24-qubit energy+gradient phase")
+    ap.add_argument("--fp64-check", action="store_true",
+                    help="also evaluate the step with the complex128 state and report |dE|")
     ap.add_argument("--served", type=int, default=48, help="requests in the served-stream phase (0: skip)")
     ap.add_argument("--served-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s)")
     args = ap.parse_args()
@@ -324,6 +326,19 @@ def main():
                "includes": "Hamiltonian and ansatz handles from host arrays (schedules, table uploads), "
                            "angle LUT upload, all kernels, energy read-back"}
 
+    fp64_check = None
+    if args.fp64_check and rank == 0:
+        # the same step with the complex128 state (FP64 amplitudes) as the GPU reference
+        del work
+        torch.cuda.empty_cache()
+        t = time.perf_counter()
+        e128, _, w128 = q2.vqe_energy_grad(ans, ham, theta, dtype="complex128", want_grad=False)
+        fp64_check = {"energy_complex128": e128, "energy_complex64": e, "abs_dE": abs(e - e128),
+                      "complex128_step_s": time.perf_counter() - t,
+                      "state_bytes_complex128": 16 * (1 << n)}
+        del w128
+        torch.cuda.empty_cache()
+
     grad = None if args.no_grad or rank != 0 else grad_phase(q2, torch)
     served = None if args.served <= 0 or rank != 0 else served_phase(q2, args.served, args.served_rate)
 
@@ -352,6 +367,7 @@ def main():
                             "hbm_gbs_read": float(state_bytes * (per[0, 4] - 1) / (expect_ms / 1000.0) / 1e9)},
             "roofline": roofline,
             "grad": grad,
+            "fp64_check": fp64_check,
             "served": served,
             "cpu_baseline": cpu,
             "e2e": e2e,
