@@ -175,11 +175,23 @@ def cpu_oracle_sample(n, n_elec, seconds=15.0, seed=0):
     return k * (1 << n) / dt, c_oracle.threads(), k
 
 
+def workload_config(name, dtype, ws, w):
+    """The `config` object of both arms' JSON lines."""
+    n, ne = w.n, w.n_elec
+    return {"workload": f"{name}: {n} qubits, {ne} electrons, {w.ansatz.n_rot} UCCSD rotations (random "
+                        f"excitation order), {w.ham.n_terms}-term JW Hamiltonian energy",
+            "state": f"{dtype} (f32 pairs, f64 reductions)" if dtype == "complex64" else f"{dtype} (f64)",
+            "parallelism": f"replicas x{ws}", "l2": "state (2^n amplitudes) larger than L2"}
+
+
 def run_reference(args, ws, rank):
     """--impl reference: the oracle (plain C, host cores) on a bounded sample."""
     if rank != 0:
         return 0
-    n_w, ne_w = WORKLOADS[args.workload][:2]
+    from synth.workloads import sweep32
+    n_w, ne_w, n_rot, min_terms = WORKLOADS[args.workload]
+    config = workload_config(args.workload, args.dtype, ws,
+                             sweep32(seed=0, n=n_w, n_elec=ne_w, n_rot=n_rot, min_terms=min_terms))
     n = min(n_w, 28)
     ne = n // 2
     for _ in range(args.warmup):
@@ -198,7 +210,7 @@ def run_reference(args, ws, rank):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample_qubits": n},
+        "config": config,
         "cpu_baseline": {"value": value, "unit": "amp-updates/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "amp-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -354,11 +366,8 @@ def main():
             "metric": "amp_updates_per_s", "value": value, "unit": "amp-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64" if args.dtype == "complex64" else "c128", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {n} qubits, {ne} electrons, {w.ansatz.n_rot} UCCSD "
-                                   f"rotations (random excitation order), {w.ham.n_terms}-term JW "
-                                   f"Hamiltonian energy", "state": args.dtype,
-                       "parallelism": f"replicas x{ws}", "l2": "state (2^n amplitudes) larger than L2"},
+            "dtype": "f32" if args.dtype == "complex64" else "f64", "data": "synthetic",
+            "config": workload_config(args.workload, args.dtype, ws, w),
             "energy": e,
             "sweep": {"ms_per_step": sweep_ms, "kernels_per_step": int(sweep_launches),
                       "amp_updates_per_s": units_per_step / (sweep_ms / 1000.0),
