@@ -189,6 +189,25 @@ q2_status q2_vqe_energy_grad(const q2_ansatz *ansatz, const q2_ham *ham, const d
                              void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /*
+ * Operator-pool gradients at U(theta)|HF>: grad_out[k] = Im <lambda|P_k|psi>
+ * with psi = U(theta)|HF> and lambda = H psi, for the Pauli strings
+ * P_k = (pool_x[k], pool_z[k]), k < n_pool.  This is dE/dphi of a rotation
+ * exp(-i phi/2 P_k) appended to the circuit, at phi = 0: the screening step
+ * of adaptive ansatz growth (the operator pools of Sec. "Variational quantum
+ * circuit ansatz"), computed with the reverse-mode machinery of Algorithm 1
+ * (the pool strings are grouped by xmask and read in one pass per group
+ * span, without changing psi or lambda).  *energy_out = <psi|H|psi>/<psi|psi>.
+ * theta: host, n_params doubles; pool_x, pool_z: host, n_pool masks (bits < n);
+ * grad_out: host, n_pool doubles.  workspace_dev: at least
+ * q2_vqe_workspace_bytes(ansatz, dtype, 1) bytes, 256-byte aligned.  The
+ * pool's tables are built and freed on `stream` by the call.  Synchronizes
+ * the stream.
+ */
+q2_status q2_pool_gradients(const q2_ansatz *ansatz, const q2_ham *ham, const double *theta, q2_dtype dtype,
+                            int64_t n_pool, const uint64_t *pool_x, const uint64_t *pool_z, double *energy_out,
+                            double *grad_out, void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
  * Batched evaluation of many small problems in one launch (the serving
  * path): request b uses ansatz[b], ham[b], theta[b] (host pointer to
  * n_params doubles) and want_grad[b]; every ansatz must have n <= 12.

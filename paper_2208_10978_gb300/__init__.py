@@ -61,6 +61,7 @@ _SIGS = {
     "q2_batch_energy_grad": ([_I, _P, _P, _P, _P, _I, _P, _P, _P, _SZ, _P], _I),
     "q2_set_tile_qubits": ([_I, _I], _I),
     "q2_expectation_noalloc": ([_P, _I, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P], _I),
+    "q2_pool_gradients": ([_P, _P, _P, _I, _I64, _P, _P, ctypes.POINTER(_D), _P, _P, _SZ, _P], _I),
 }
 
 
@@ -298,6 +299,28 @@ def vqe_energy_grad(ansatz, ham, theta, dtype="complex64", want_grad=True, works
                                     ctypes.byref(e), _np_ptr(g) if want_grad else None,
                                     ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                     _stream_ptr()))
+    return e.value, g, workspace
+
+
+def pool_gradients(ansatz, ham, theta, pool_x, pool_z, dtype="complex64", workspace=None):
+    """Operator-pool screening: (E, g, workspace) with g[k] = Im <H psi|P_k|psi> at
+    psi = U(theta)|HF>, i.e. dE/dphi of exp(-i phi/2 P_k) appended at phi = 0.
+    Synchronizes the current stream."""
+    d = _dtype_code(dtype)
+    theta = _f64(theta)
+    if len(theta) != ansatz.n_params:
+        raise ValueError("theta has the wrong length")
+    px, pz = _u64(pool_x), _u64(pool_z)
+    if len(px) != len(pz):
+        raise ValueError("pool masks must have equal length")
+    need = ansatz.workspace_bytes(d, True)
+    if workspace is None or workspace.numel() < need:
+        workspace = alloc_workspace(need)
+    e = _D()
+    g = np.zeros(len(px))
+    _check(lib().q2_pool_gradients(ansatz.handle, ham.handle, _np_ptr(theta), d, len(px), _np_ptr(px),
+                                   _np_ptr(pz), ctypes.byref(e), _np_ptr(g),
+                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr()))
     return e.value, g, workspace
 
 

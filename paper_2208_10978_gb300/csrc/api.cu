@@ -778,6 +778,118 @@ q2_status q2_vqe_energy_grad(const q2_ansatz *ansatz, const q2_ham *ham, const d
                                             workspace_dev, workspace_bytes, st);
 }
 
+}  // extern "C"
+
+namespace {
+
+// ---- operator-pool gradients: Im<lambda|P_k|psi> for a list of Pauli strings at the final state
+
+template <typename R>
+q2_status pool_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_dtype d, int64_t n_pool,
+                    const uint64_t *px, const uint64_t *pz, double *energy_out, double *pool_out, void *ws,
+                    size_t ws_bytes, cudaStream_t st) {
+  const RotPlan *rp;
+  const DevTables *rt;
+  q2_status s = ansatz_tables(a, d, &rp, &rt);
+  if (s != Q2_OK) return s;
+  const HamPlan *hp;
+  const DevTables *ht;
+  if ((s = ham_tables(h, d, &hp, &ht)) != Q2_OK) return s;
+  const int n = a->n;
+  const WsLayout L = ws_layout(n, d, 1, rp->lut_entries, (int64_t)a->x.size());
+  if (ws_bytes < L.total) return fail(Q2_ERR_INVALID, "workspace too small");
+  RotPlan pp;
+  try {
+    pp = build_rot_plan(n, n_pool, px, pz, tile_bits(d), g_chunk[d]);
+  } catch (const std::exception &e) {
+    return fail(Q2_ERR_INVALID, std::string("pool schedule: ") + e.what());
+  }
+  unsigned char *base = static_cast<unsigned char *>(ws);
+  R *psi = reinterpret_cast<R *>(base + L.psi);
+  R *lam = reinterpret_cast<R *>(base + L.lam);
+  double *partial = reinterpret_cast<double *>(base + L.partial);
+  double *out = reinterpret_cast<double *>(base + L.out);
+  // forward: psi = U(theta)|HF>, lambda = H psi, E
+  const size_t nrot = a->x.size();
+  std::vector<double> phi(nrot);
+  for (size_t k = 0; k < nrot; ++k) phi[k] = a->coef[k] * theta[a->param[k]];
+  std::vector<double> lut2(2 * (size_t)std::max<int64_t>(1, rp->lut_entries));
+  rp->build_lut(phi.data(), lut2.data());
+  std::vector<unsigned char> lb = lut_bytes(lut2, d);
+  Q2_CUDA(cudaMemcpyAsync(base + L.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice, st), "upload LUT");
+  Q2_CUDA(launch_init_hf<R>(psi, n, a->n_elec, st), "init_hf");
+  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, rt->blocks, base + L.lut, st), "sweep");
+  Q2_CUDA(run_happly<R>(psi, lam, n, *hp, *ht, st), "H apply");
+  const int dgrid = dot_grid<R>(n);
+  Q2_CUDA(launch_dot<R>(psi, lam, n, partial, dgrid, st), "dot");
+  Q2_CUDA(launch_reduce_pairs(partial, dgrid, out, st), "reduce");
+  // pool strings as rotations of angle 0 (cos = 1, sin = 0): the reverse sweep reads
+  // Im<lambda|P_k|psi> for each and leaves psi and lambda unchanged
+  std::vector<double> zero(std::max<int64_t>(1, n_pool), 0.0);
+  std::vector<double> plut(2 * (size_t)std::max<int64_t>(1, pp.lut_entries));
+  pp.build_lut(zero.data(), plut.data());
+  std::vector<unsigned char> plb = lut_bytes(plut, d);
+  const size_t o_groups = 0;
+  const size_t o_sm = align_up(o_groups + sizeof(GroupDesc) * std::max<size_t>(1, pp.groups.size()), 256);
+  const size_t o_lut = align_up(o_sm + sizeof(uint64_t) * std::max<size_t>(1, pp.signmask.size()), 256);
+  const size_t o_g = align_up(o_lut + plb.size(), 256);
+  const size_t total = o_g + sizeof(double) * (size_t)std::max<int64_t>(1, n_pool);
+  unsigned char *tmp = nullptr;
+  Q2_CUDA(cudaMallocAsync((void **)&tmp, total, st), "cudaMallocAsync(pool tables)");
+  cudaError_t e = cudaSuccess;
+  if (!pp.groups.empty())
+    e = cudaMemcpyAsync(tmp + o_groups, pp.groups.data(), sizeof(GroupDesc) * pp.groups.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !pp.signmask.empty())
+    e = cudaMemcpyAsync(tmp + o_sm, pp.signmask.data(), sizeof(uint64_t) * pp.signmask.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + o_lut, plb.data(), plb.size(), cudaMemcpyHostToDevice, st);
+  double *gpool = reinterpret_cast<double *>(tmp + o_g);
+  for (size_t i = pp.passes.size(); e == cudaSuccess && i-- > 0;)
+    e = launch_reverse<R>(psi, lam, n, pp.passes[i], reinterpret_cast<const GroupDesc *>(tmp + o_groups), nullptr,
+                          false, tmp + o_lut, reinterpret_cast<const uint64_t *>(tmp + o_sm),
+                          static_cast<const R *>(rt->wlut), partial, gpool, st);
+  double host_out[2] = {0, 0};
+  unsigned waits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && n_pool)
+    e = cudaMemcpyAsync(pool_out, gpool, sizeof(double) * (size_t)n_pool, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = read_wait_timeouts_async(&waits, st);
+  cudaFreeAsync(tmp, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "pool gradients");
+  if (waits) {
+    clear_wait_timeouts(st);
+    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
+  }
+  *energy_out = host_out[0] / host_out[1];
+  return Q2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+q2_status q2_pool_gradients(const q2_ansatz *ansatz, const q2_ham *ham, const double *theta, q2_dtype dtype,
+                            int64_t n_pool, const uint64_t *pool_x, const uint64_t *pool_z, double *energy_out,
+                            double *grad_out, void *workspace_dev, size_t workspace_bytes, void *stream) {
+  if (!ansatz || !ham || !energy_out || (n_pool > 0 && (!pool_x || !pool_z || !grad_out)))
+    return fail(Q2_ERR_INVALID, "NULL argument");
+  if (n_pool < 0) return fail(Q2_ERR_INVALID, "negative pool size");
+  q2_status s = check_n(ansatz->n, dtype);
+  if (s != Q2_OK) return s;
+  if (ham->n != ansatz->n) return fail(Q2_ERR_INVALID, "Hamiltonian and ansatz qubit counts differ");
+  if ((s = check_finite(ansatz->n_params, theta, "theta")) != Q2_OK) return s;
+  if ((s = check_masks(ansatz->n, n_pool, pool_x, pool_z, "pool")) != Q2_OK) return s;
+  if (!workspace_dev || !aligned(workspace_dev, 256))
+    return fail(Q2_ERR_INVALID, "workspace must be a 256-byte aligned device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return dtype == Q2_C64 ? pool_impl<float>(ansatz, ham, theta, dtype, n_pool, pool_x, pool_z, energy_out,
+                                            grad_out, workspace_dev, workspace_bytes, st)
+                         : pool_impl<double>(ansatz, ham, theta, dtype, n_pool, pool_x, pool_z, energy_out,
+                                             grad_out, workspace_dev, workspace_bytes, st);
+}
+
 size_t q2_batch_workspace_bytes(int n_requests, const q2_ansatz *const *ansatz, const q2_ham *const *ham,
                                 q2_dtype dtype) {
   if (n_requests < 0 || (n_requests > 0 && (!ansatz || !ham)) || !valid_dtype(dtype)) return 0;

@@ -190,6 +190,24 @@ def test_vqe_gradient_generic_rotations(dtype, shared):
     assert np.max(np.abs(g - g_ref)) < (1e-9 if dtype == "complex128" else 1e-4)
 
 
+@pytest.mark.parametrize("kind", ["spin_conserving", "paper_spin_adapted"])
+def test_excitation_set_variants(kind):
+    """The spin-conserving and the paper's spin-adapted generator sets (Sec. "Variational
+    quantum circuit ansatz", Table 1) run through the same kernels: energy and dE/dtheta
+    against the oracle in complex128 and complex64."""
+    w = uccsd_energy(10, 4, seed=5, kind=kind)
+    a = w.ansatz
+    ans = q2.Ansatz.from_uccsd(a)
+    ham = q2.Hamiltonian(10, w.ham.x, w.ham.z, w.ham.c)
+    theta = np.random.default_rng(8).normal(0, 0.3, size=a.n_params)
+    e_ref, gphi = c_oracle.energy_and_gradient(10, 4, a.x, a.z, a.angles(theta), w.ham.x, w.ham.z, w.ham.c)
+    g_ref = sv.fold_to_theta(gphi, a.param, a.coef, a.n_params)
+    for dtype, tol_g in (("complex128", 1e-9), ("complex64", 1e-4)):
+        e, g, _ = q2.vqe_energy_grad(ans, ham, theta, dtype=dtype, want_grad=True)
+        assert abs(e - e_ref) < TOL_E[dtype]
+        assert np.max(np.abs(g - g_ref)) < tol_g
+
+
 def test_autograd_function():
     w = uccsd_energy(8, 4, seed=3)
     ans = q2.Ansatz.from_uccsd(w.ansatz)
@@ -209,3 +227,30 @@ def test_errors_are_loud():
         q2.apply_pauli_rotations(psi, 8, [1 << 8], [0], [0.1])
     with pytest.raises(q2.Q2Error):
         q2.state_init_hf(psi, 8, 9)
+
+
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+def test_pool_gradients_match_oracle(dtype):
+    """Operator-pool screening: Im<H psi|P_k|psi> for a pool of UCCSD generator strings
+    (a different excitation set than the ansatz) plus random strings, against the oracle."""
+    from synth.uccsd import uccsd_rotations
+    n, ne = 11, 5
+    w = uccsd_energy(10, 4, seed=6)
+    a = w.ansatz
+    ans = q2.Ansatz(n, ne, a.x, a.z, a.param, a.coef, a.n_params)
+    ham = q2.Hamiltonian(n, np.concatenate([w.ham.x, [1 << 10]]).astype(np.uint64),
+                         np.concatenate([w.ham.z, [0]]).astype(np.uint64), np.concatenate([w.ham.c, [0.4]]))
+    pool = uccsd_rotations(n, ne, "spin_conserving")
+    rng = np.random.default_rng(21)
+    px = np.concatenate([pool.x, rng.integers(0, 1 << n, size=40).astype(np.uint64), [0]]).astype(np.uint64)
+    pz = np.concatenate([pool.z, rng.integers(0, 1 << n, size=40).astype(np.uint64), [5]]).astype(np.uint64)
+    theta = rng.normal(0, 0.3, size=a.n_params)
+    e, g, _ = q2.pool_gradients(ans, ham, theta, px, pz, dtype=dtype)
+    hx = np.concatenate([w.ham.x, [1 << 10]]).astype(np.uint64)
+    hz = np.concatenate([w.ham.z, [0]]).astype(np.uint64)
+    hc = np.concatenate([w.ham.c, [0.4]])
+    psi = sv.apply_rotations(sv.hf_state(n, ne), a.x, a.z, a.angles(theta))
+    lam = sv.apply_hamiltonian(psi, hx, hz, hc)
+    g_ref = np.array([np.imag(np.vdot(lam, sv.apply_pauli(psi, x, z))) for x, z in zip(px, pz)])
+    assert abs(e - sv.expectation(psi, hx, hz, hc) / np.vdot(psi, psi).real) < TOL_E[dtype]
+    assert np.max(np.abs(g - g_ref)) < (1e-10 if dtype == "complex128" else 1e-4)
