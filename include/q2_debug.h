@@ -62,6 +62,16 @@ int q2_debug_threads_per_cta(void);
 q2_status q2_debug_enable_timing(int enable);
 q2_status q2_debug_last_timing(double *out8);
 
+/*
+ * Failure-path check of the bounded device waits: launches one CTA that
+ * waits, with `polls` polls (1..2^22), on an mbarrier that nothing completes
+ * -- the situation of a tile copy that never lands.  The wait gives up,
+ * the kernel returns, and the call reports it exactly as the compute calls
+ * do: Q2_ERR_TIMEOUT (and the device counter is cleared).  Q2_OK would mean
+ * the give-up path is broken.  Synchronizes the stream.
+ */
+q2_status q2_debug_wait_probe(unsigned polls, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1060,6 +1060,20 @@ q2_status q2_debug_enable_timing(int enable) {
   return Q2_OK;
 }
 
+q2_status q2_debug_wait_probe(unsigned polls, void *stream) {
+  if (polls == 0 || polls > (1u << 22)) return fail(Q2_ERR_INVALID, "polls must be in 1..2^22");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned waits = 0;
+  Q2_CUDA(launch_wait_probe(polls, st), "wait probe");
+  Q2_CUDA(read_wait_timeouts_async(&waits, st), "D2H");
+  Q2_CUDA(cudaStreamSynchronize(st), "sync");
+  if (waits) {
+    Q2_CUDA(clear_wait_timeouts(st), "clear");
+    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
+  }
+  return Q2_OK;
+}
+
 q2_status q2_debug_last_timing(double *out8) {
   if (!out8) return fail(Q2_ERR_INVALID, "NULL output");
   if (!g_timing.valid) return fail(Q2_ERR_INVALID, "no timed call on this thread");

@@ -254,8 +254,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < WAIT_POLLS; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t polls = WAIT_POLLS) {
+  for (uint32_t i = 0; i < polls; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -1706,6 +1706,21 @@ PassDesc worst_pass(int T, int C) {
 }
 
 }  // namespace
+
+// Probe of the bounded wait: an mbarrier that nothing completes (one pending
+// arrival, no copies), waited on with `polls` polls; the wait gives up and
+// records itself exactly like a tile-copy wait that never completes.
+__global__ void k_wait_probe(uint32_t polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, polls);
+}
+
+cudaError_t launch_wait_probe(uint32_t polls, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(polls);
+  return cudaGetLastError();
+}
 
 cudaError_t read_wait_timeouts_async(unsigned *host, cudaStream_t st) {
   return cudaMemcpyFromSymbolAsync(host, g_wait_timeouts, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);

@@ -14,6 +14,7 @@ cudaError_t launch_reduce_pairs(const double *partial, int nblocks, double *out,
 // Bounded device waits that gave up (bulk tile copies), counted since the last clear.
 cudaError_t read_wait_timeouts_async(unsigned *host, cudaStream_t st);
 cudaError_t clear_wait_timeouts(cudaStream_t st);
+cudaError_t launch_wait_probe(uint32_t polls, cudaStream_t st);
 
 template <typename R> cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st);
 template <typename R>

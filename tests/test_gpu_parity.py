@@ -254,3 +254,23 @@ def test_pool_gradients_match_oracle(dtype):
     g_ref = np.array([np.imag(np.vdot(lam, sv.apply_pauli(psi, x, z))) for x, z in zip(px, pz)])
     assert abs(e - sv.expectation(psi, hx, hz, hc) / np.vdot(psi, psi).real) < TOL_E[dtype]
     assert np.max(np.abs(g - g_ref)) < (1e-10 if dtype == "complex128" else 1e-4)
+
+
+def test_device_wait_gives_up_and_context_survives():
+    """A bounded device wait on an mbarrier that nothing completes gives up, the call
+    reports Q2_ERR_TIMEOUT, and the context stays usable for the next evaluation."""
+    import ctypes
+    L = q2.lib()
+    L.q2_debug_wait_probe.argtypes = [ctypes.c_uint, ctypes.c_void_p]
+    L.q2_debug_wait_probe.restype = ctypes.c_int
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.q2_debug_wait_probe(1000, stream) == q2.Q2_ERR_TIMEOUT
+    assert L.q2_debug_wait_probe(0, stream) == q2.Q2_ERR_INVALID
+    w = uccsd_energy(10, 4, seed=2)
+    a = w.ansatz
+    ans = q2.Ansatz.from_uccsd(a)
+    ham = q2.Hamiltonian(10, w.ham.x, w.ham.z, w.ham.c)
+    e, _, _ = q2.vqe_energy_grad(ans, ham, w.theta, dtype="complex64", want_grad=False)
+    psi = sv.apply_rotations(sv.hf_state(10, 4), a.x, a.z, a.angles(w.theta))
+    e_ref, _ = sv.energy(psi, w.ham.x, w.ham.z, w.ham.c)
+    assert abs(e - e_ref) < TOL_E["complex64"]
