@@ -1,29 +1,34 @@
 // Tile kernels of the state-vector engine (sm_103a).
 //
 // Every kernel here is HBM-streaming: a persistent grid walks the 2^(n-T)
-// tiles of one pass; each CTA gathers a tile (2^(T-C) chunks of 2^C
-// contiguous amplitudes) into shared memory with 16-byte loads, applies all
-// groups of the pass there, and writes the tile back (or only reduces it).
-// Tiles are cosets of the pass's local subspace W (see q2_internal.h), so a
-// pass touches every amplitude exactly once and tiles never overlap.  The
-// pass's offsets, group and block descriptors and LUT are staged in shared
-// memory once per CTA.
+// tiles of one pass; each CTA brings a tile (2^(T-C) chunks of 2^C
+// contiguous amplitudes) into shared memory -- by bulk async copies counted
+// on an mbarrier for tiles of 2^9 amplitudes and more, by 16-byte loads
+// below that -- applies all groups of the pass there, and writes the tile
+// back (or only reduces it).  Tiles are cosets of the pass's local subspace
+// W (see q2_internal.h), so a pass touches every amplitude exactly once and
+// tiles never overlap.  The pass's offsets, group and block descriptors and
+// LUT are staged in shared memory once per CTA.
 //
-// Sweep and expectation work on register blocks: for each block of groups
-// whose xmasks span d local dimensions, a thread loads a 2^d-amplitude coset
-// into registers, applies (or evaluates) every group of the block there with
-// compile-time pair indices, and writes it back once.  H apply and the
-// reverse sweep walk one group at a time (pair q = tid + NT*j).  Codes come
-// from host tables plus one per-tile code per group.
+// The main kernels work on register blocks: for each block of groups whose
+// xmasks span d local dimensions, a thread loads a 2^d-amplitude coset into
+// registers, applies (or evaluates) every group of the block there with
+// compile-time pair indices, and writes it back once.  The fallbacks
+// (k_happly, k_reverse) walk one group at a time (pair q = tid + NT*j).
+// Codes come from host tables plus one per-tile code per group.
 //
-//   k_init_hf     HF determinant (Eq. jw-wfn-map)
-//   k_sweep       rotation groups in order (product formula after Eq. ucc)
-//   k_expect      sum_t c_t <psi|P_t|psi> and <psi|psi> (Eq. qubit-ham-detail)
-//   k_happly      lambda = H psi (Algorithm 1, start of the backward pass)
-//   k_dot         Re<psi|lambda>, <psi|psi>
-//   k_reverse     Algorithm 1's reverse loop over one pass: per-rotation
-//                 Im<lambda|P_k|psi>, then psi and lambda un-rotated together
-//   k_reduce_*    fixed-order reductions of per-CTA partials (deterministic)
+//   k_init_hf       HF determinant (Eq. jw-wfn-map)
+//   k_sweep         rotation groups in order (product formula after Eq. ucc)
+//   k_expect        sum_t c_t <psi|P_t|psi> and <psi|psi> (Eq. qubit-ham-detail)
+//   k_happly_blk    lambda = H psi (Algorithm 1, start of the backward pass);
+//                   k_happly for tiles below 2^9 amplitudes
+//   k_dot           Re<psi|lambda>, <psi|psi>
+//   k_reverse_blk   Algorithm 1's reverse loop over one pass of one-parameter
+//                   groups (complex64): per-group weighted Im<lambda|P|psi>
+//                   sums, then psi and lambda un-rotated together;
+//                   k_reverse (per-rotation sums) for every other pass
+//   k_reduce_*      fixed-order reductions of per-CTA partials (deterministic)
+//   k_wait_probe    the bounded-wait give-up path, for the failure test
 #include <cuda_runtime.h>
 
 #include <cstdint>
