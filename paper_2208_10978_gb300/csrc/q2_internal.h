@@ -55,15 +55,21 @@ constexpr int D_MAX = 4;         // max span dimension of a register block (rota
 constexpr int D_MAX_EXPECT = 3;  // max span dimension of a Hamiltonian register block
 
 // Register blocks.  Consecutive groups of a pass whose xmasks span d <= D_MAX
-// local dimensions form a block.  The block's span V (basis v_1..v_d in
-// reduced echelon form, pivots = highest bits) splits a tile into 2^(T-d)
-// cosets; thread tid takes cosets s = tid + NT*j, whose amplitudes are the
-// local indices base(s) ^ comb[c] (c < 2^d), base(s) = s with zero bits
-// inserted at the pivots.  A thread keeps one coset in registers while it
-// applies every group of the block; a group with xmask coordinates a in V
-// pairs combo c with c ^ a.  The code of an amplitude is the XOR of a tile
-// part (computed once per tile) and host-tabulated parts for the lane, the
-// warp, the coset j and the combo c, all linear in the local index.
+// local dimensions form a block.  The block's span V has as basis v_1..v_d
+// the groups' own xmasks in order of appearance (so a group that opens a
+// dimension pairs along one basis bit); the pivots are the highest bits of
+// V's echelon rows, on which the basis is invertible.  V splits a tile into
+// 2^(T-d) cosets; thread tid takes cosets s = tid + NT*j, whose amplitudes
+// are the local indices base(s) ^ comb[c] (c < 2^d), base(s) = s with zero
+// bits inserted at the pivots.  A thread keeps one coset in registers while
+// it applies every group of the block; a group with xmask coordinates a in V
+// pairs combo c with c ^ a.  A block is canonical (BlockDesc::canon = d)
+// when its first d groups pair along bits 0..d-1 and are REAL; kernels
+// unroll those.  The code of an amplitude is the XOR of a tile part
+// (computed once per tile) and host-tabulated parts for the lane, the warp,
+// the coset j and the combo c, all linear in the local index.  Group LUTs
+// start at multiples of their 2^r entries (passes at multiples of the
+// largest), so kernels reach an entry by XOR of the code into its offset.
 struct alignas(16) GroupDesc {
   uint64_t bp[R_MAX];      // code basis in packed-index space
   uint32_t xl;             // xmask in local-index space (0 for diagonal groups)
