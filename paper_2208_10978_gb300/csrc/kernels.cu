@@ -187,6 +187,16 @@ __device__ __forceinline__ void tile_codes(const Stage<R, E> &s, int ng, uint64_
 
 __device__ __forceinline__ uint64_t tile_base(uint64_t t, uint64_t umask) { return deposit_bits(t, umask); }
 
+// Tile bases of a persistent CTA (tiles blockIdx.x, + gridDim.x, ...): the
+// deposit of t + gridDim.x is the deposit of t plus that of gridDim.x with
+// the carry passed across the bits outside the mask, so each step is one add.
+struct TileWalk {
+  uint64_t base, step, mask;
+  __device__ __forceinline__ TileWalk(uint64_t t0, uint64_t stride, uint64_t m)
+      : base(deposit_bits(t0, m)), step(deposit_bits(stride, m)), mask(m) {}
+  __device__ __forceinline__ void next() { base = ((base | ~mask) + step) & mask; }
+};
+
 // Gather one tile of `src` into shared memory (LOAD_BATCH 16-byte loads in flight per thread).
 #ifndef Q2_LOAD_BATCH
 #define Q2_LOAD_BATCH 4
@@ -590,8 +600,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     uint32_t parity = 0;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const uint64_t base = tile_base(t, pd.umask);
+    TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
+      const uint64_t base = tw.base;
       bulk_load_tile(psi, base, st, tile, &bar);
       tile_codes(st, ng, t);
       const bool ok = mbar_wait(&bar, parity);
@@ -816,13 +827,14 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *
   if (!GUARD && threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t parity = 0;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
     if constexpr (GUARD) {
-      load_tile<R, STREAM>(psi, tile_base(t, pd.umask), st, reinterpret_cast<V *>(tile));
+      load_tile<R, STREAM>(psi, tw.base, st, reinterpret_cast<V *>(tile));
       tile_codes(st, ng, t);
       __syncthreads();
     } else {
-      bulk_load_tile(psi, tile_base(t, pd.umask), st, tile, &bar);
+      bulk_load_tile(psi, tw.base, st, tile, &bar);
       tile_codes(st, ng, t);
       const bool ok = mbar_wait(&bar, parity);
       parity ^= 1u;
@@ -1139,8 +1151,9 @@ __global__ void __launch_bounds__(NT, 2) k_happly_blk(const R *psi, R *lam, int 
   const uint32_t nch = 1u << (pd.T - pd.C);
   const uint32_t bytes = (uint32_t)sizeof(C2) << pd.C;
   uint32_t parity = 0;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t base = tile_base(t, pd.umask);
+  TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
+    const uint64_t base = tw.base;
     if (threadIdx.x == 0) mbar_expect_tx(&bar, (first_pass ? 1u : 2u) * bytes * nch);
     for (uint32_t h = threadIdx.x; h < nch; h += NT) {
       const uint64_t gi = base ^ st.off[h];
@@ -1566,8 +1579,9 @@ __global__ void __launch_bounds__(NT, 2) k_reverse_blk(float *psi, float *lam, i
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
   uint32_t parity = 0;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t base = tile_base(t, pd.umask);
+  TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
+    const uint64_t base = tw.base;
     const uint32_t nch = 1u << (pd.T - pd.C);
     const uint32_t bytes = (uint32_t)sizeof(float2) << pd.C;
     if (threadIdx.x == 0) mbar_expect_tx(&bar, 2 * bytes * nch);
