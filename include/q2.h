@@ -155,14 +155,15 @@ q2_status q2_apply_hamiltonian(const void *psi_dev, void *lam_dev, int n, q2_dty
  * with phi_j = coef[j] * theta[param_idx[j]], applied in order j = 0..n_rot-1
  * to |HF> with n_elec electrons (Eq. ucc after the JW mapping and the
  * first-order Trotter product).  Host arrays of n_rot entries, copied;
- * param_idx values in [0, n_params).  The pass schedule is built once here.
+ * param_idx values in [0, n_params).  The pass schedule, the gradient
+ * weights and the device tables are built once per dtype, at first use.
  */
 q2_status q2_ansatz_create(int n, int n_elec, int64_t n_rot, const uint64_t *x, const uint64_t *z,
                            const int32_t *param_idx, const double *coef, int32_t n_params,
                            q2_ansatz **out);
 q2_status q2_ansatz_destroy(q2_ansatz *ansatz);
 
-/* Number of HBM passes of the ansatz's rotation schedule for a dtype. */
+/* Number of HBM passes and of rotation groups of the ansatz's schedule for a dtype. */
 q2_status q2_ansatz_info(const q2_ansatz *ansatz, q2_dtype dtype, int64_t *n_passes,
                          int64_t *n_groups);
 
