@@ -46,6 +46,18 @@ q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uin
                             int64_t *counts, void *passes, void *groups, void *blocks,
                             double *lut2);
 
+/*
+ * Gradient tables of an ansatz's rotation schedule (the ones q2_vqe_energy_grad
+ * uses): the groups of q2_debug_rot_plan with one_param and wlut set, the
+ * weights w_g(code) = sum_k coef_k sign_k(code) of every one-parameter group
+ * (*n_weights doubles in total, group g's at its wlut offset) and per
+ * rotation the factor that folds its reverse-sweep sum into dE/dtheta
+ * (n_rot doubles).  Output arrays may be NULL (sizes only).
+ */
+q2_status q2_debug_rot_weights(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, const int32_t *param,
+                               const double *coef, int tile_qubits, int chunk_qubits, int64_t *n_weights,
+                               void *groups, double *wlut, double *fold);
+
 /* Threads per CTA of the tile kernels (the per-thread offsets of q2_group.jcode use it). */
 int q2_debug_threads_per_cta(void);
 

@@ -1027,6 +1027,27 @@ q2_status q2_debug_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint6
   return Q2_OK;
 }
 
+q2_status q2_debug_rot_weights(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, const int32_t *param,
+                               const double *coef, int tile_qubits, int chunk_qubits, int64_t *n_weights,
+                               void *groups, double *wlut, double *fold) {
+  if (n < 1 || n > 34 || !n_weights || (n_rot > 0 && (!param || !coef))) return fail(Q2_ERR_INVALID, "bad arguments");
+  if (tile_qubits < 1 || tile_qubits > T_LIMIT || chunk_qubits < 1) return fail(Q2_ERR_INVALID, "bad tile shape");
+  q2_status s = check_masks(n, n_rot, x, z, "rotations");
+  if (s != Q2_OK) return s;
+  RotPlan p;
+  try {
+    p = build_rot_plan(n, n_rot, x, z, tile_qubits, chunk_qubits);
+    set_param_weights(p, param, coef);
+  } catch (const std::exception &e) {
+    return fail(Q2_ERR_INVALID, e.what());
+  }
+  *n_weights = (int64_t)p.wlut.size();
+  if (groups) std::memcpy(groups, p.groups.data(), sizeof(GroupDesc) * p.groups.size());
+  if (wlut) std::memcpy(wlut, p.wlut.data(), sizeof(double) * p.wlut.size());
+  if (fold) std::memcpy(fold, p.fold.data(), sizeof(double) * p.fold.size());
+  return Q2_OK;
+}
+
 q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z, const double *coef,
                             int tile_qubits, int chunk_qubits, int64_t *counts, void *passes, void *groups,
                             void *blocks, double *lut2) {

@@ -300,3 +300,70 @@ def reverse(psi, lam, n, passes, groups, lut, signmask, NT):
         psi[idx] = tp
         lam[idx] = tl
     return psi, lam, g_out
+
+
+def rot_weights(lib, n, x, z, param, coef, T, C, n_groups):
+    """Gradient tables of an ansatz schedule: (groups with one_param/wlut, weights, fold)."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    param = np.ascontiguousarray(param, dtype=np.int32)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    f = lib.q2_debug_rot_weights
+    f.argtypes = [ctypes.c_int, ctypes.c_int64] + [ctypes.c_void_p] * 4 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 4
+    f.restype = ctypes.c_int
+    nw = np.zeros(1, dtype=np.int64)
+    assert f(n, len(x), _p(x), _p(z), _p(param), _p(coef), T, C, _p(nw), None, None, None) == 0
+    groups = np.zeros(n_groups, dtype=GROUP_DT)
+    wl = np.zeros(max(1, int(nw[0])))
+    fold = np.zeros(max(1, len(x)))
+    assert f(n, len(x), _p(x), _p(z), _p(param), _p(coef), T, C, _p(nw), _p(groups), _p(wl), _p(fold)) == 0
+    return groups, wl, fold
+
+
+def reverse_weighted(psi, lam, n, passes, groups, lut, signmask, wlut, NT):
+    """Reverse sweep as the kernels run it with gradient weights: a one-parameter
+    group adds sum_pairs w(code) val at its first rotation, other groups per rotation."""
+    psi, lam = psi.copy(), lam.copy()
+    g_out = np.zeros(int(passes["rot_end"].max()) if len(passes) else 0)
+    for pi in range(len(passes) - 1, -1, -1):
+        pd = passes[pi]
+        T = int(pd["T"])
+        idx = tile_index(n, pd)
+        tp, tl = psi[idx], lam[idx]
+        for gi in range(pd["g_end"] - 1, pd["g_begin"] - 1, -1):
+            g = groups[gi]
+            kind = int(g["kind"])
+            P, li, lane, warp = _pair_layout(g, T, NT)
+            code = _pair_codes(g, P, lane, warp, _tilecode(g, T, tp.shape[0]))
+            cs = lut[int(g["lut"]) + code]
+            c, s = cs[..., 0], -cs[..., 1]
+            k0 = int(pd["rot_begin"]) + int(g["rot0"])
+            if kind == DIAG:
+                a, b = tp[:, li], tl[:, li]
+                val = (np.conj(b) * a).imag
+            else:
+                lj = li ^ int(g["xl"])
+                pa, pb, la, lb = tp[:, li], tp[:, lj], tl[:, li], tl[:, lj]
+                if kind == REAL:
+                    val = (np.conj(lb) * pa - np.conj(la) * pb).real
+                else:
+                    val = (np.conj(la) * pb + np.conj(lb) * pa).imag
+            if int(g["one_param"]):
+                g_out[k0] += float(np.sum(wlut[int(g["wlut"]) + code] * val))
+            else:
+                for k in range(int(g["m"])):
+                    sign = 1.0 - 2.0 * ((signmask[k0 + k].astype(np.uint64) >> code.astype(np.uint64))
+                                        & np.uint64(1)).astype(np.float64)
+                    g_out[k0 + k] += float(np.sum(sign * val))
+            if kind == DIAG:
+                tp[:, li] = (c - 1j * s) * a
+                tl[:, li] = (c - 1j * s) * b
+            elif kind == REAL:
+                tp[:, li], tp[:, lj] = c * pa - s * pb, s * pa + c * pb
+                tl[:, li], tl[:, lj] = c * la - s * lb, s * la + c * lb
+            else:
+                tp[:, li], tp[:, lj] = c * pa - 1j * s * pb, c * pb - 1j * s * pa
+                tl[:, li], tl[:, lj] = c * la - 1j * s * lb, c * lb - 1j * s * la
+        psi[idx] = tp
+        lam[idx] = tl
+    return psi, lam, g_out

@@ -224,6 +224,55 @@ def test_schedule_reverse_gradient(lib, n, ne, T, C):
     assert np.max(np.abs(psi_b - sv.hf_state(n, ne))) < 1e-12
 
 
+@pytest.mark.parametrize("n,ne,T,C", [(8, 4, 6, 2), (10, 5, 8, 3)])
+def test_gradient_weights_match_oracle(lib, n, ne, T, C):
+    """Gradient tables of the kernels (one-parameter group weights, fold factors):
+    the reverse sweep emulated with them gives the oracle's dE/dtheta for an ansatz
+    that mixes runs sharing one parameter with per-rotation parameters, over every
+    group kind (x = 0, odd and even Y counts)."""
+    rng = np.random.default_rng(40 + n)
+    w = uccsd_energy(n, ne, seed=7)
+    x, z, _ = _random_rotations(rng, n, 70)
+    run = np.cumsum(np.concatenate([[0], (x[1:] != x[:-1]).astype(np.int64)]))
+    shared = rng.random(run.max() + 1) < 0.5            # half the runs share one parameter
+    param = np.where(shared[run], run, run.max() + 1 + np.arange(len(x)))
+    _, param = np.unique(param, return_inverse=True)
+    param = param.astype(np.int32)
+    n_params = int(param.max()) + 1
+    coef = rng.choice([-1.0, -0.25, 0.5, 1.0], size=len(x))
+    theta = rng.normal(0, 0.5, size=n_params)
+    phi = coef * theta[param]
+    e_ref, gphi = sv.energy_and_gradient(n, ne, x, z, phi, w.ham.x, w.ham.z, w.ham.c)
+    g_ref = sv.fold_to_theta(gphi, param, coef, n_params)
+    NT = lib.q2_debug_threads_per_cta()
+    passes, groups, blocks, lut, sm = emu.rot_plan(lib, n, x, z, phi, T, C)
+    wgroups, wl, fold = emu.rot_weights(lib, n, x, z, param, coef, T, C, len(groups))
+    assert np.any(wgroups["one_param"] == 1) and np.any(wgroups["one_param"] == 0)
+    hp, hg, hb, hl = emu.ham_plan(lib, n, w.ham.x, w.ham.z, w.ham.c, T, C)
+    psi = emu.sweep(sv.hf_state(n, ne), n, passes, groups, blocks, lut, NT)
+    lam = emu.happly(psi, n, hp, hg, hl, NT)
+    _, _, g_rot = emu.reverse_weighted(psi, lam, n, passes, wgroups, lut, sm, wl, NT)
+    g = np.zeros(n_params)
+    np.add.at(g, param, fold[:len(x)] * g_rot)
+    assert np.max(np.abs(g - g_ref)) < 1e-11
+
+
+def test_canonical_blocks(lib):
+    """A block marked canonical has its first d groups pairing along bits 0..d-1, REAL."""
+    from synth.workloads import sweep32
+    w = sweep32(0, n=20, n_elec=10, n_rot=3000, min_terms=2000)
+    a = w.ansatz
+    for plan in (emu.rot_plan(lib, 20, a.x, a.z, a.angles(w.theta), 12, 4),
+                 emu.ham_plan(lib, 20, w.ham.x, w.ham.z, w.ham.c, 13, 4)):
+        passes, groups, blocks = plan[0], plan[1], plan[2]
+        assert np.mean(blocks["canon"] == blocks["d"]) > 0.5
+        for pd in passes:
+            for b in blocks[pd["b_begin"]:pd["b_end"]]:
+                for k in range(int(b["canon"])):
+                    g = groups[pd["g_begin"] + int(b["g_begin"]) + k]
+                    assert int(g["a"]) == 1 << k and int(g["kind"]) == emu.REAL
+
+
 def test_schedule_fusion_depth_32_qubits(lib):
     """On the 32-qubit random-order workload, one pass holds many excitations."""
     from synth import excitations
