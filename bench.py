@@ -234,7 +234,10 @@ def main():
                     help="also evaluate the step with the complex128 state and report |dE|")
     ap.add_argument("--served", type=int, default=48, help="requests in the served-stream phase (0: skip)")
     ap.add_argument("--served-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--served-child", nargs=2, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.served_child:
+        return served_child(*args.served_child)
     ws, rank, local = dist_env()
 
     if args.impl == "reference":
@@ -352,7 +355,7 @@ def main():
         torch.cuda.empty_cache()
 
     grad = None if args.no_grad or rank != 0 else grad_phase(q2, torch)
-    served = None if args.served <= 0 or rank != 0 else served_phase(q2, args.served, args.served_rate)
+    served = None if args.served <= 0 or rank != 0 else served_isolated(args.served, args.served_rate, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -433,6 +436,33 @@ def served_phase(q2, n_requests, rate):
             "p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"], "mean_latency_s": st["mean_s"],
             "hbm_high_water_bytes": st["high_water_bytes"], "budget_bytes": 150 * 10**9,
             "dtype": "c64 state, f64 reductions", "problem_generation_s_excluded": gen_s}
+
+
+def served_isolated(n_requests, rate, local, timeout_s=900):
+    """served_phase in a fresh interpreter with its own CUDA context, so that a failure
+    there cannot reach the step measurement; returns its dict or {"error": ...}."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--served-child", str(n_requests), str(rate)]
+    env = dict(os.environ, LOCAL_RANK=str(local), WORLD_SIZE="1", RANK="0")
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, env=env)
+    except subprocess.TimeoutExpired:
+        return {"error": f"served phase did not finish within {timeout_s} s"}
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        tail = (r.stderr.strip().splitlines() or ["no output"])[-1]
+        return {"error": f"served phase exited {r.returncode}: {tail[:300]}"}
+    try:
+        return json.loads(lines[-1])
+    except ValueError as exc:
+        return {"error": f"served phase printed no result: {exc}"}
+
+
+def served_child(n_requests, rate):
+    import torch
+    import paper_2208_10978_gb300 as q2
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps(served_phase(q2, int(n_requests), float(rate))), flush=True)
+    return 0
 
 
 def plan_bytes(lib, w, dtype):

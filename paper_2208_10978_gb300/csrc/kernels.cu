@@ -32,6 +32,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "q2_internal.h"
 #include "kernels.h"
@@ -1684,11 +1687,23 @@ size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry
   return o;
 }
 
+// The shared-memory attribute is per-function state shared by every host
+// thread: it is set once per device and function, under a lock, so no
+// launch on another thread ever overlaps a change of it.
 template <typename K>
 cudaError_t prepare(K kernel, size_t smem_cap) {
-  if (smem_cap > 48 * 1024)
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
-  return cudaSuccess;
+  if (smem_cap <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const std::pair<int, const void *> key(dev, reinterpret_cast<const void *>(kernel));
+  std::lock_guard<std::mutex> g(mu);
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
 }
 
 unsigned grid_for(uint64_t ntiles, int per_sm) {

@@ -14,6 +14,9 @@
 // result does not depend on the rest of the batch.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <set>
+
 #include "small.h"
 
 namespace q2 {
@@ -230,11 +233,21 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int max_qubits, in
   if (n_items <= 0) return cudaSuccess;
   const size_t smem = sizeof(C2) * ((size_t)1 << max_qubits) * (any_grad ? 2 : 1);
   auto k = k_batch<R>;
-  // per-function attribute shared by all host threads: always the largest size any batch needs
+  // per-function attribute shared by all host threads: the largest size any batch needs, set once
+  // per device under a lock so that no launch on another thread overlaps a change of it
   const size_t smem_cap = sizeof(C2) * ((size_t)1 << SMALL_MAX_QUBITS) * 2;
   if (smem_cap > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+    static std::mutex mu;
+    static std::set<int> done;
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
     if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    if (!done.count(d)) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+      if (e != cudaSuccess) return e;
+      done.insert(d);
+    }
   }
   int per_sm = 1, dev = 0, sms = 1;
   cudaGetDevice(&dev);

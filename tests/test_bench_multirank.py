@@ -59,3 +59,14 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.max_over_ranks(12.5, None) == 12.5
     assert bench.whole_job_rate(1, 2, 1e6, 1000.0) == pytest.approx(2e6)
+
+
+def test_served_phase_failure_is_reported_not_raised():
+    """The served phase runs in a child process; its failure comes back as an error field
+    (here: no CUDA device on this machine) and leaves the caller unaffected."""
+    if torch.cuda.is_available():
+        pytest.skip("checks the failure path on a machine without a GPU")
+    sys.path.insert(0, ROOT)
+    import bench
+    out = bench.served_isolated(2, 2.0, 0, timeout_s=240)
+    assert set(out) == {"error"} and "exited" in out["error"]
