@@ -284,3 +284,33 @@ def test_schedule_fusion_depth_32_qubits(lib):
     rots_per_pass = a.n_rot / len(passes)
     assert len(groups) == 200
     assert rots_per_pass > 40          # one tile dimension per excitation
+
+
+def test_tile_walk_masked_add():
+    """Persistent CTAs walk tile bases by one masked add per step: the deposit of
+    t + g equals ((deposit(t) | ~mask) + deposit(g)) & mask while t + g < 2^popcount(mask)."""
+    def deposit(v, m):
+        out, k = 0, 0
+        while m:
+            low = m & -m
+            if (v >> k) & 1:
+                out |= low
+            k += 1
+            m &= m - 1
+        return out
+    full = (1 << 64) - 1
+    rng = np.random.default_rng(12)
+    for _ in range(300):
+        n = int(rng.integers(9, 35))
+        T = int(rng.integers(8, min(13, n) + 1))
+        m = 0
+        for b in rng.choice(n, size=n - T, replace=False):
+            m |= 1 << int(b)
+        ntiles = 1 << (n - T)
+        g = int(rng.integers(1, 1200))
+        t = int(rng.integers(0, g))
+        base, step = deposit(t, m), deposit(g, m)
+        while t < ntiles:
+            assert base == deposit(t, m)
+            base = ((base | (~m & full)) + step) & m
+            t += g
