@@ -310,6 +310,15 @@ def test_tile_walk_masked_add():
         g = int(rng.integers(1, 1200))
         t = int(rng.integers(0, g))
         base, step = deposit(t, m), deposit(g, m)
+        for _ in range(64):                     # the first steps and, below, the last ones
+            if t >= ntiles:
+                break
+            assert base == deposit(t, m)
+            base = ((base | (~m & full)) + step) & m
+            t += g
+        k = max(0, (ntiles - 1 - t) // g - 8)   # jump close to the end and walk out of the range
+        t += k * g
+        base = deposit(t, m)
         while t < ntiles:
             assert base == deposit(t, m)
             base = ((base | (~m & full)) + step) & m
