@@ -37,9 +37,14 @@
  * documented as optional, a misaligned device pointer, or a workspace that
  * is too small.  Q2_ERR_CUDA wraps launch and driver errors, Q2_ERR_OOM a
  * failed device allocation.  Q2_ERR_TIMEOUT: a bounded device-side wait for
- * a tile copy gave up (the kernel stops instead of spinning); the calls that
- * read results back (q2_expectation, q2_expectation_noalloc,
- * q2_vqe_energy_grad) report it, and results of such a call are not valid.
+ * a tile copy gave up (the kernel stops instead of spinning) and the results
+ * of that call are not valid.  Each call that reads results back
+ * (q2_expectation, q2_expectation_noalloc, q2_vqe_energy_grad,
+ * q2_pool_gradients) counts its own give-ups in a fault word of its own
+ * (in its workspace or temporary memory), so calls running concurrently on
+ * other streams or threads never see each other's timeouts.  The
+ * asynchronous calls (q2_apply_pauli_rotations, q2_apply_hamiltonian) count
+ * give-ups in one per-device word that q2_async_status reads and clears.
  */
 #ifndef Q2_H
 #define Q2_H
@@ -101,6 +106,16 @@ q2_status q2_ham_create(int n, const uint64_t *x, const uint64_t *z, const doubl
                         int64_t n_terms, q2_ham **out);
 q2_status q2_ham_destroy(q2_ham *ham);
 
+/*
+ * Timeouts of the asynchronous calls: synchronizes `stream`, then reads and
+ * clears the count of bounded device waits that gave up in kernels of
+ * q2_apply_pauli_rotations and q2_apply_hamiltonian on the current device
+ * (all streams and host threads share this one count).  Returns
+ * Q2_ERR_TIMEOUT if any did since the last check (the states those calls
+ * wrote are then not valid), Q2_OK otherwise.
+ */
+q2_status q2_async_status(void *stream);
+
 /* Number of terms and of distinct xmask groups of a Hamiltonian handle. */
 q2_status q2_ham_info(const q2_ham *ham, int64_t *n_terms, int64_t *n_groups);
 
@@ -125,18 +140,22 @@ q2_status q2_expectation(const void *psi_dev, int n, q2_dtype dtype, const q2_ha
  * Where q2_expectation takes temporary device memory, this call uses one
  * fixed library buffer of Q2_NOALLOC_SCRATCH_BYTES (4 MiB): a static device
  * array that every GPU which loads the library holds until the process
- * exits.  It receives the per-CTA partial sums, the two result slots and a
- * copy of the Hamiltonian's group, block and LUT tables (uploaded on every
- * call, so the handle's own device tables are not needed).
+ * exits.  It receives the per-CTA partial sums, the two result slots, the
+ * call's fault word and a copy of the Hamiltonian's group, block and LUT
+ * tables (uploaded on every call, so the handle's own device tables are not
+ * needed).
  * Arguments and results are those of q2_expectation.  Extra error:
  * Q2_ERR_INVALID if the tables and partial sums do not fit the buffer (the
  * message gives the bytes needed); nothing is launched then.  The first call
- * on a device looks up the buffer's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream
- * capture.  Every call shares the buffer, which keeps the last call's
- * contents (nothing in it needs to start at zero): calls that can overlap on
- * the GPU (other streams, other host threads on the same device) race, and
- * the caller must serialize them.  Synchronizes `stream`.
+ * in each CUDA context (that is, the first call on each device, and again
+ * after that device's context has been destroyed and created anew) looks up
+ * the buffer's device address with cudaGetSymbolAddress, with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the buffer, which keeps the last call's contents; a call clears the
+ * parts that must start at zero (result slots and fault word) itself, on its
+ * stream.  Calls that can overlap on the GPU (other streams, other host
+ * threads on the same device) race, and the caller must serialize them.
+ * Synchronizes `stream`.
  */
 #define Q2_NOALLOC_SCRATCH_BYTES (4u << 20)
 q2_status q2_expectation_noalloc(const void *psi_dev, int n, q2_dtype dtype, const q2_ham *ham,
@@ -167,7 +186,25 @@ q2_status q2_ansatz_destroy(q2_ansatz *ansatz);
 q2_status q2_ansatz_info(const q2_ansatz *ansatz, q2_dtype dtype, int64_t *n_passes,
                          int64_t *n_groups);
 
-/* Bytes of device workspace q2_vqe_energy_grad needs for this ansatz. */
+/*
+ * Device bytes of the resident tables a handle uploads for `dtype` at its
+ * first use by the tile kernels (the host schedule is built if needed):
+ * group and register-block descriptors and the LUT of combined coefficients
+ * for a Hamiltonian; group and block descriptors, sign masks and gradient
+ * weights for an ansatz.  *per_call_bytes (may be NULL) receives the bytes of
+ * the angle LUT that every q2_vqe_energy_grad call uploads.  Used for memory
+ * accounting (the request loop charges resident tables to its budget) and to
+ * count host-to-device traffic.
+ */
+q2_status q2_ham_table_bytes(const q2_ham *ham, q2_dtype dtype, size_t *device_bytes);
+q2_status q2_ansatz_table_bytes(const q2_ansatz *ansatz, q2_dtype dtype, size_t *device_bytes,
+                                size_t *per_call_bytes);
+
+/*
+ * Bytes of device workspace q2_vqe_energy_grad needs for this ansatz.  It takes
+ * the ansatz rather than (n, dtype, want_grad) because the workspace also
+ * holds the per-call angle LUT, whose size depends on the ansatz's schedule.
+ */
 size_t q2_vqe_workspace_bytes(const q2_ansatz *ansatz, q2_dtype dtype, int want_grad);
 
 /*

@@ -79,10 +79,18 @@ q2_status q2_debug_last_timing(double *out8);
  * waits, with `polls` polls (1..2^22), on an mbarrier that nothing completes
  * -- the situation of a tile copy that never lands.  The wait gives up,
  * the kernel returns, and the call reports it exactly as the compute calls
- * do: Q2_ERR_TIMEOUT (and the device counter is cleared).  Q2_OK would mean
- * the give-up path is broken.  Synchronizes the stream.
+ * do: Q2_ERR_TIMEOUT, counted in a fault word of this call's own (so
+ * concurrent calls on other streams are not affected).  Q2_OK would mean the
+ * give-up path is broken.  Synchronizes the stream.
  */
 q2_status q2_debug_wait_probe(unsigned polls, void *stream);
+
+/*
+ * Measured FP64 fused multiply-add throughput of the current device in flop/s
+ * (one launch of independent FMA chains on every SM, timed with CUDA events on
+ * `stream`): the denominator of the complex128 sweep's FP64-ALU roofline.
+ */
+q2_status q2_debug_fp64_rate(double *flops_per_s, void *stream);
 
 #ifdef __cplusplus
 }

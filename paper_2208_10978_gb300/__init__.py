@@ -62,6 +62,9 @@ _SIGS = {
     "q2_set_tile_qubits": ([_I, _I], _I),
     "q2_expectation_noalloc": ([_P, _I, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P], _I),
     "q2_pool_gradients": ([_P, _P, _P, _I, _I64, _P, _P, ctypes.POINTER(_D), _P, _P, _SZ, _P], _I),
+    "q2_async_status": ([_P], _I),
+    "q2_ham_table_bytes": ([_P, _I, ctypes.POINTER(_SZ)], _I),
+    "q2_ansatz_table_bytes": ([_P, _I, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)], _I),
 }
 
 
@@ -189,6 +192,12 @@ class Hamiltonian:
                                     _stream_ptr()))
         return e.value, nrm.value
 
+    def table_bytes(self, dtype="complex64"):
+        """Device bytes of this Hamiltonian's resident tables for a state dtype."""
+        b = _SZ()
+        _check(lib().q2_ham_table_bytes(self._h, _dtype_code(dtype), ctypes.byref(b)))
+        return b.value
+
     def apply(self, psi, lam):
         """lam <- H psi."""
         p, d = _state_args(psi, self.n)
@@ -241,6 +250,12 @@ class Ansatz:
         p, g = _I64(), _I64()
         _check(lib().q2_ansatz_info(self._a, _dtype_code(dtype), ctypes.byref(p), ctypes.byref(g)))
         return p.value, g.value
+
+    def table_bytes(self, dtype="complex64"):
+        """(resident device table bytes, angle-LUT bytes uploaded per evaluation) for a state dtype."""
+        b, c = _SZ(), _SZ()
+        _check(lib().q2_ansatz_table_bytes(self._a, _dtype_code(dtype), ctypes.byref(b), ctypes.byref(c)))
+        return b.value, c.value
 
     def workspace_bytes(self, dtype="complex64", want_grad=False):
         b = lib().q2_vqe_workspace_bytes(self._a, _dtype_code(dtype), 1 if want_grad else 0)
@@ -355,6 +370,12 @@ def batch_energy_grad(ansatze, hams, thetas, want_grads, dtype="complex64", work
     _check(lib().q2_batch_energy_grad(nb, A, H, TH, wg, d, _np_ptr(e), G, ctypes.c_void_p(workspace.data_ptr()),
                                       workspace.numel(), _stream_ptr()))
     return e, grads, workspace
+
+
+def async_status():
+    """Raise Q2Error(Q2_ERR_TIMEOUT) if a kernel of apply_pauli_rotations or Hamiltonian.apply
+    gave up a bounded wait since the last check (synchronizes the current stream)."""
+    _check(lib().q2_async_status(_stream_ptr()))
 
 
 def set_tile_qubits(dtype, t):

@@ -163,6 +163,10 @@ struct q2_ham {
   std::mutex mu;
 };
 
+namespace q2 {
+q2_status ham_host_plan(const q2_ham *hc, q2_dtype d, const HamPlan **plan, int *chunk);
+}
+
 struct q2_ansatz {
   int n = 0, n_elec = 0;
   int32_t n_params = 0;
@@ -281,9 +285,9 @@ q2_status ansatz_tables(const q2_ansatz *ac, q2_dtype d, const RotPlan **plan, c
 
 template <typename R>
 cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups, const BlockDesc *dblocks,
-                      const void *dlut, cudaStream_t st) {
+                      const void *dlut, unsigned *fault, cudaStream_t st) {
   for (const PassDesc &pd : p.passes) {
-    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dblocks, dlut, st);
+    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dblocks, dlut, fault, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -291,18 +295,20 @@ cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups,
 
 template <typename R>
 cudaError_t run_expect(const R *psi, int n, const HamPlan &h, const DevTables &t, double *partial,
-                       int grid, double *out2, cudaStream_t st) {
+                       int grid, double *out2, unsigned *fault, cudaStream_t st) {
   for (size_t i = 0; i < h.passes.size(); ++i) {
-    cudaError_t e = launch_expect<R>(psi, n, h.passes[i], t.groups, t.blocks, t.lut, partial, grid, i == 0, st);
+    cudaError_t e =
+        launch_expect<R>(psi, n, h.passes[i], t.groups, t.blocks, t.lut, partial, grid, i == 0, fault, st);
     if (e != cudaSuccess) return e;
   }
   return launch_reduce_pairs(partial, grid, out2, st);
 }
 
 template <typename R>
-cudaError_t run_happly(const R *psi, R *lam, int n, const HamPlan &h, const DevTables &t, cudaStream_t st) {
+cudaError_t run_happly(const R *psi, R *lam, int n, const HamPlan &h, const DevTables &t, unsigned *fault,
+                       cudaStream_t st) {
   for (size_t i = 0; i < h.passes.size(); ++i) {
-    cudaError_t e = launch_happly<R>(psi, lam, n, h.passes[i], t.groups, t.blocks, t.lut, i == 0, st);
+    cudaError_t e = launch_happly<R>(psi, lam, n, h.passes[i], t.groups, t.blocks, t.lut, i == 0, fault, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -313,9 +319,20 @@ int partial_doubles(int grad) {
   return grad ? blocks * RP_MAX : blocks * 2;
 }
 
+// Workspace of q2_vqe_energy_grad / q2_pool_gradients: psi, lambda, the
+// per-call angle LUT, dE/dphi, CTA partials and a 32-byte result block
+// (out[0] <psi|H|psi>, out[1] <psi|psi>, then the call's fault word).
 struct WsLayout {
   size_t psi, lam, lut, gphi, partial, out, total;
 };
+
+// The fault word of a 4-double result block (after the two sums).
+unsigned *fault_word(double *out4) { return reinterpret_cast<unsigned *>(out4 + 2); }
+unsigned fault_of(const double *host4) {
+  unsigned f;
+  std::memcpy(&f, host4 + 2, sizeof f);
+  return f;
+}
 
 WsLayout ws_layout(int n, q2_dtype d, int grad, int64_t lut_entries, int64_t n_rot) {
   WsLayout L;
@@ -364,30 +381,27 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
   std::vector<double> lut2(2 * (size_t)std::max<int64_t>(1, rp->lut_entries));
   rp->build_lut(phi.data(), lut2.data());
   std::vector<unsigned char> lb = lut_bytes(lut2, d);
+  Q2_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 4, st), "clear results");
   Q2_CUDA(cudaMemcpyAsync(base + L.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice, st), "upload LUT");
+  unsigned *fault = fault_word(out);
 
   const bool timing = g_timing.enabled;
   g_timing.valid = false;
   if (timing) Q2_CUDA(g_timing.ensure(), "timing events");
   Q2_CUDA(launch_init_hf<R>(psi, n, a->n_elec, st), "init_hf");
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[0], st), "event");
-  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, rt->blocks, base + L.lut, st), "sweep");
+  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, rt->blocks, base + L.lut, fault, st), "sweep");
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[1], st), "event");
-  double host_out[2] = {0, 0};
+  double host_out[4] = {0, 0, 0, 0};
   g_timing.counts[0] = (double)rp->passes.size();
   g_timing.counts[3] = (double)((size_t)amp_bytes(d) << n);
   if (!want_grad) {
     const int grid = expect_grid<R>(n, hp->T, std::min(g_chunk[d], hp->T));
-    Q2_CUDA(run_expect<R>(psi, n, *hp, *ht, partial, grid, out, st), "expectation");
+    Q2_CUDA(run_expect<R>(psi, n, *hp, *ht, partial, grid, out, fault, st), "expectation");
     if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[2], st), "event");
-    unsigned waits = 0;
     Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
-    Q2_CUDA(read_wait_timeouts_async(&waits, st), "D2H");
     Q2_CUDA(cudaStreamSynchronize(st), "sync");
-    if (waits) {
-      clear_wait_timeouts(st);
-      return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
-    }
+    if (fault_of(host_out)) return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
     *energy_out = host_out[0] / host_out[1];
     if (timing) {
       g_timing.counts[1] = (double)hp->passes.size() + 1;
@@ -398,14 +412,15 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
     }
     return Q2_OK;
   }
-  Q2_CUDA(run_happly<R>(psi, lam, n, *hp, *ht, st), "H apply");
+  Q2_CUDA(run_happly<R>(psi, lam, n, *hp, *ht, fault, st), "H apply");
   const int dgrid = dot_grid<R>(n);
   Q2_CUDA(launch_dot<R>(psi, lam, n, partial, dgrid, st), "dot");
   Q2_CUDA(launch_reduce_pairs(partial, dgrid, out, st), "reduce");
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[2], st), "event");
   for (size_t i = rp->passes.size(); i-- > 0;) {
     Q2_CUDA(launch_reverse<R>(psi, lam, n, rp->passes[i], rt->groups, rt->blocks, rp->pass_one_param[i] != 0,
-                              base + L.lut, rt->signmask, static_cast<const R *>(rt->wlut), partial, gphi, st),
+                              base + L.lut, rt->signmask, static_cast<const R *>(rt->wlut), partial, gphi, fault,
+                              st),
             "reverse sweep");
   }
   if (timing) Q2_CUDA(cudaEventRecord(g_timing.ev[3], st), "event");
@@ -417,15 +432,10 @@ q2_status vqe_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2_
     g_timing.valid = true;
   }
   std::vector<double> g(nrot);
-  unsigned waits = 0;
   Q2_CUDA(cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st), "D2H");
   if (nrot) Q2_CUDA(cudaMemcpyAsync(g.data(), gphi, sizeof(double) * nrot, cudaMemcpyDeviceToHost, st), "D2H");
-  Q2_CUDA(read_wait_timeouts_async(&waits, st), "D2H");
   Q2_CUDA(cudaStreamSynchronize(st), "sync");
-  if (waits) {
-    clear_wait_timeouts(st);
-    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
-  }
+  if (fault_of(host_out)) return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
   *energy_out = host_out[0] / host_out[1];
   for (int p = 0; p < a->n_params; ++p) grad_out[p] = 0.0;
   for (size_t k = 0; k < nrot; ++k) grad_out[a->param[k]] += rp->fold[k] * g[k];
@@ -606,8 +616,9 @@ q2_status q2_apply_pauli_rotations(void *psi_dev, int n, q2_dtype dtype, const u
   if (e == cudaSuccess) {
     const GroupDesc *dg = reinterpret_cast<const GroupDesc *>(tmp);
     const BlockDesc *db = reinterpret_cast<const BlockDesc *>(tmp + gb);
-    e = dtype == Q2_C64 ? run_sweep<float>(static_cast<float *>(psi_dev), n, p, dg, db, tmp + gb + bb, st)
-                        : run_sweep<double>(static_cast<double *>(psi_dev), n, p, dg, db, tmp + gb + bb, st);
+    e = dtype == Q2_C64
+            ? run_sweep<float>(static_cast<float *>(psi_dev), n, p, dg, db, tmp + gb + bb, nullptr, st)
+            : run_sweep<double>(static_cast<double *>(psi_dev), n, p, dg, db, tmp + gb + bb, nullptr, st);
   }
   cudaFreeAsync(tmp, st);
   if (e != cudaSuccess) return cuda_fail(e, "apply_pauli_rotations");
@@ -643,6 +654,15 @@ q2_status q2_ham_destroy(q2_ham *ham) {
   return Q2_OK;
 }
 
+q2_status q2_async_status(void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned host = 0;
+  Q2_CUDA(take_async_faults(&host, st), "read asynchronous fault count");
+  Q2_CUDA(cudaStreamSynchronize(st), "sync");
+  if (host) return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy of an asynchronous call timed out");
+  return Q2_OK;
+}
+
 q2_status q2_ham_info(const q2_ham *ham, int64_t *n_terms, int64_t *n_groups) {
   if (!ham) return fail(Q2_ERR_INVALID, "NULL handle");
   if (n_terms) *n_terms = (int64_t)ham->c.size();
@@ -663,23 +683,23 @@ q2_status q2_expectation(const void *psi_dev, int n, q2_dtype dtype, const q2_ha
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int C = std::min(g_chunk[dtype], hp->T);
   const int grid = dtype == Q2_C64 ? expect_grid<float>(n, hp->T, C) : expect_grid<double>(n, hp->T, C);
+  // [partials 2 * grid][result block of 4 doubles: sums, fault word]
   double *tmp = nullptr;
-  Q2_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * (2 * (size_t)grid + 2), st), "cudaMallocAsync(partials)");
-  double host_out[2] = {0, 0};
-  cudaError_t e =
-      dtype == Q2_C64
-          ? run_expect<float>(static_cast<const float *>(psi_dev), n, *hp, *ht, tmp, grid, tmp + 2 * grid, st)
-          : run_expect<double>(static_cast<const double *>(psi_dev), n, *hp, *ht, tmp, grid, tmp + 2 * grid, st);
-  unsigned waits = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp + 2 * grid, sizeof(host_out), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = read_wait_timeouts_async(&waits, st);
+  Q2_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * (2 * (size_t)grid + 4), st), "cudaMallocAsync(partials)");
+  double *out4 = tmp + 2 * grid;
+  double host_out[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemsetAsync(out4, 0, sizeof(double) * 4, st);
+  if (e == cudaSuccess)
+    e = dtype == Q2_C64 ? run_expect<float>(static_cast<const float *>(psi_dev), n, *hp, *ht, tmp, grid, out4,
+                                            fault_word(out4), st)
+                        : run_expect<double>(static_cast<const double *>(psi_dev), n, *hp, *ht, tmp, grid, out4,
+                                             fault_word(out4), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, out4, sizeof(host_out), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(tmp, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const cudaError_t es = cudaStreamSynchronize(st);   // always: nothing may still use tmp or host_out
+  if (e == cudaSuccess) e = es;
   if (e != cudaSuccess) return cuda_fail(e, "expectation");
-  if (waits) {
-    clear_wait_timeouts(st);
-    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
-  }
+  if (fault_of(host_out)) return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
   *energy_out = host_out[0] / host_out[1];
   if (norm_out) *norm_out = host_out[1];
   return Q2_OK;
@@ -699,8 +719,10 @@ q2_status q2_apply_hamiltonian(const void *psi_dev, void *lam_dev, int n, q2_dty
   if ((s = ham_tables(ham, dtype, &hp, &ht)) != Q2_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = dtype == Q2_C64
-                      ? run_happly<float>(static_cast<const float *>(psi_dev), static_cast<float *>(lam_dev), n, *hp, *ht, st)
-                      : run_happly<double>(static_cast<const double *>(psi_dev), static_cast<double *>(lam_dev), n, *hp, *ht, st);
+                      ? run_happly<float>(static_cast<const float *>(psi_dev), static_cast<float *>(lam_dev), n, *hp,
+                                          *ht, nullptr, st)
+                      : run_happly<double>(static_cast<const double *>(psi_dev), static_cast<double *>(lam_dev), n,
+                                           *hp, *ht, nullptr, st);
   if (e != cudaSuccess) return cuda_fail(e, "apply_hamiltonian");
   return Q2_OK;
 }
@@ -750,6 +772,35 @@ q2_status q2_ansatz_info(const q2_ansatz *ansatz, q2_dtype dtype, int64_t *n_pas
   if (s != Q2_OK) return s;
   if (n_passes) *n_passes = (int64_t)rp->passes.size();
   if (n_groups) *n_groups = (int64_t)rp->groups.size();
+  return Q2_OK;
+}
+
+q2_status q2_ham_table_bytes(const q2_ham *ham, q2_dtype dtype, size_t *device_bytes) {
+  if (!ham || !device_bytes) return fail(Q2_ERR_INVALID, "NULL argument");
+  if (!valid_dtype(dtype)) return fail(Q2_ERR_INVALID, "unknown dtype");
+  const HamPlan *hp;
+  int chunk = 0;
+  q2_status s = ham_host_plan(ham, dtype, &hp, &chunk);
+  if (s != Q2_OK) return s;
+  *device_bytes = sizeof(GroupDesc) * std::max<size_t>(1, hp->groups.size()) +
+                  sizeof(BlockDesc) * std::max<size_t>(1, hp->blocks.size()) +
+                  std::max<size_t>(16, hp->lut2.size() * (size_t)(amp_bytes(dtype) / 2));
+  return Q2_OK;
+}
+
+q2_status q2_ansatz_table_bytes(const q2_ansatz *ansatz, q2_dtype dtype, size_t *device_bytes,
+                                size_t *per_call_bytes) {
+  if (!ansatz || !device_bytes) return fail(Q2_ERR_INVALID, "NULL argument");
+  if (!valid_dtype(dtype)) return fail(Q2_ERR_INVALID, "unknown dtype");
+  const RotPlan *rp;
+  q2_status s = ansatz_tables(ansatz, dtype, &rp, nullptr);
+  if (s != Q2_OK) return s;
+  const size_t real = (size_t)amp_bytes(dtype) / 2;
+  *device_bytes = sizeof(GroupDesc) * std::max<size_t>(1, rp->groups.size()) +
+                  sizeof(BlockDesc) * std::max<size_t>(1, rp->blocks.size()) +
+                  sizeof(uint64_t) * std::max<size_t>(1, rp->signmask.size()) +
+                  real * std::max<size_t>(1, rp->wlut.size());
+  if (per_call_bytes) *per_call_bytes = (size_t)amp_bytes(dtype) * (size_t)std::max<int64_t>(1, rp->lut_entries);
   return Q2_OK;
 }
 
@@ -816,10 +867,12 @@ q2_status pool_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2
   std::vector<double> lut2(2 * (size_t)std::max<int64_t>(1, rp->lut_entries));
   rp->build_lut(phi.data(), lut2.data());
   std::vector<unsigned char> lb = lut_bytes(lut2, d);
+  Q2_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 4, st), "clear results");
+  unsigned *fault = fault_word(out);
   Q2_CUDA(cudaMemcpyAsync(base + L.lut, lb.data(), lb.size(), cudaMemcpyHostToDevice, st), "upload LUT");
   Q2_CUDA(launch_init_hf<R>(psi, n, a->n_elec, st), "init_hf");
-  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, rt->blocks, base + L.lut, st), "sweep");
-  Q2_CUDA(run_happly<R>(psi, lam, n, *hp, *ht, st), "H apply");
+  Q2_CUDA(run_sweep<R>(psi, n, *rp, rt->groups, rt->blocks, base + L.lut, fault, st), "sweep");
+  Q2_CUDA(run_happly<R>(psi, lam, n, *hp, *ht, fault, st), "H apply");
   const int dgrid = dot_grid<R>(n);
   Q2_CUDA(launch_dot<R>(psi, lam, n, partial, dgrid, st), "dot");
   Q2_CUDA(launch_reduce_pairs(partial, dgrid, out, st), "reduce");
@@ -848,20 +901,16 @@ q2_status pool_impl(const q2_ansatz *a, const q2_ham *h, const double *theta, q2
   for (size_t i = pp.passes.size(); e == cudaSuccess && i-- > 0;)
     e = launch_reverse<R>(psi, lam, n, pp.passes[i], reinterpret_cast<const GroupDesc *>(tmp + o_groups), nullptr,
                           false, tmp + o_lut, reinterpret_cast<const uint64_t *>(tmp + o_sm),
-                          static_cast<const R *>(rt->wlut), partial, gpool, st);
-  double host_out[2] = {0, 0};
-  unsigned waits = 0;
+                          static_cast<const R *>(rt->wlut), partial, gpool, fault, st);
+  double host_out[4] = {0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && n_pool)
     e = cudaMemcpyAsync(pool_out, gpool, sizeof(double) * (size_t)n_pool, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = read_wait_timeouts_async(&waits, st);
   cudaFreeAsync(tmp, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const cudaError_t es = cudaStreamSynchronize(st);   // always: nothing may still use tmp or the outputs
+  if (e == cudaSuccess) e = es;
   if (e != cudaSuccess) return cuda_fail(e, "pool gradients");
-  if (waits) {
-    clear_wait_timeouts(st);
-    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
-  }
+  if (fault_of(host_out)) return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
   *energy_out = host_out[0] / host_out[1];
   return Q2_OK;
 }
@@ -1084,14 +1133,23 @@ q2_status q2_debug_enable_timing(int enable) {
 q2_status q2_debug_wait_probe(unsigned polls, void *stream) {
   if (polls == 0 || polls > (1u << 22)) return fail(Q2_ERR_INVALID, "polls must be in 1..2^22");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  unsigned waits = 0;
-  Q2_CUDA(launch_wait_probe(polls, st), "wait probe");
-  Q2_CUDA(read_wait_timeouts_async(&waits, st), "D2H");
-  Q2_CUDA(cudaStreamSynchronize(st), "sync");
-  if (waits) {
-    Q2_CUDA(clear_wait_timeouts(st), "clear");
-    return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
-  }
+  unsigned *fault = nullptr;
+  Q2_CUDA(cudaMallocAsync((void **)&fault, sizeof(unsigned), st), "cudaMallocAsync(fault word)");
+  unsigned host = 0;
+  cudaError_t e = cudaMemsetAsync(fault, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = launch_wait_probe(polls, fault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, fault, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(fault, st);
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  if (host) return fail(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
+  return Q2_OK;
+}
+
+q2_status q2_debug_fp64_rate(double *flops_per_s, void *stream) {
+  if (!flops_per_s) return fail(Q2_ERR_INVALID, "NULL output");
+  Q2_CUDA(measure_fp64_rate(flops_per_s, static_cast<cudaStream_t>(stream)), "FP64 rate probe");
   return Q2_OK;
 }
 

@@ -255,10 +255,14 @@ __device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Stage<R
 // issues one cp.async.bulk per chunk and the CTA waits on an mbarrier that
 // counts the bytes, so a CTA waiting for its tile issues no instructions and
 // the SM's other CTAs compute meanwhile.  Every wait is bounded: a wait that
-// gives up counts itself in g_wait_timeouts (read and cleared by the host),
-// and the CTA stops working on its tiles.
+// gives up adds one to the calling API function's own fault word (a device
+// word that call zeroes before its first launch and reads back with its
+// results), and the CTA stops working on its tiles.  Kernels of calls that
+// return before their work completes (q2_apply_pauli_rotations,
+// q2_apply_hamiltonian) get no fault word and count into g_async_faults,
+// which only q2_async_status reads and clears.
 
-__device__ unsigned int g_wait_timeouts;
+__device__ unsigned int g_async_faults;
 
 constexpr uint32_t WAIT_POLLS = 1u << 22;   // try_wait polls before a wait gives up
 
@@ -272,7 +276,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t polls = WAIT_POLLS) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *fault,
+                                          uint32_t polls = WAIT_POLLS) {
   for (uint32_t i = 0; i < polls; ++i) {
     uint32_t done;
     asm volatile(
@@ -282,7 +287,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
         : "memory");
     if (done) return true;
   }
-  atomicAdd(&g_wait_timeouts, 1u);
+  atomicAdd(fault ? fault : &g_async_faults, 1u);
   return false;
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -574,7 +579,7 @@ __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, co
 template <typename R, bool STREAM, int TT, bool GUARD>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
     k_sweep(R *psi, int n, PassDesc pd, const GroupDesc *groups, const BlockDesc *blocks,
-            const typename Vec2<R>::type *lut) {
+            const typename Vec2<R>::type *lut, unsigned *fault) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -608,10 +613,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
       const uint64_t base = tw.base;
       bulk_load_tile(psi, base, st, tile, &bar);
       tile_codes(st, ng, t);
-      const bool ok = mbar_wait(&bar, parity);
+      const bool ok = mbar_wait(&bar, parity, fault);
       parity ^= 1u;
       if (__syncthreads_or(!ok)) {
-        mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+        mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
         break;
       }
       for (int b = 0; b < nb; ++b) {
@@ -814,7 +819,7 @@ template <typename R, bool STREAM, int TT, bool GUARD>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *psi, int n, PassDesc pd,
                                                   const GroupDesc *groups, const BlockDesc *blocks,
                                                   const typename Vec2<R>::type *lut, double *partial,
-                                                  int first_pass) {
+                                                  int first_pass, unsigned *fault) {
   using C2 = typename Vec2<R>::type;
   using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -839,10 +844,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *
     } else {
       bulk_load_tile(psi, tw.base, st, tile, &bar);
       tile_codes(st, ng, t);
-      const bool ok = mbar_wait(&bar, parity);
+      const bool ok = mbar_wait(&bar, parity, fault);
       parity ^= 1u;
       if (__syncthreads_or(!ok)) {
-        mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+        mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
         break;
       }
     }
@@ -1139,7 +1144,8 @@ __device__ __forceinline__ void happly_block_any(const typename Vec2<R>::type *t
 template <typename R, int TT>
 __global__ void __launch_bounds__(NT, 2) k_happly_blk(const R *psi, R *lam, int n, PassDesc pd,
                                                       const GroupDesc *groups, const BlockDesc *blocks,
-                                                      const typename Vec2<R>::type *lut, int first_pass) {
+                                                      const typename Vec2<R>::type *lut, int first_pass,
+                                                      unsigned *fault) {
   using C2 = typename Vec2<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(sizeof(C2), pd, 2, 0, sizeof(C2), sizeof(C2) << R_MAX);
@@ -1166,10 +1172,10 @@ __global__ void __launch_bounds__(NT, 2) k_happly_blk(const R *psi, R *lam, int 
     if (first_pass)
       for (uint32_t l = threadIdx.x; l < st.amps; l += NT) tl[l] = C2{0, 0};
     tile_codes(st, ng, t);
-    const bool ok = mbar_wait(&bar, parity);
+    const bool ok = mbar_wait(&bar, parity, fault);
     parity ^= 1u;
     if (__syncthreads_or(!ok)) {
-      mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
       break;
     }
     for (int b = 0; b < nb; ++b) {
@@ -1559,7 +1565,8 @@ __host__ __device__ inline size_t rev_extra_bytes(int lut_count) {
 template <int TT>
 __global__ void __launch_bounds__(NT, 2) k_reverse_blk(float *psi, float *lam, int n, PassDesc pd,
                                                        const GroupDesc *groups, const BlockDesc *blocks,
-                                                       const float2 *lut, const float *wlut, double *partial) {
+                                                       const float2 *lut, const float *wlut, double *partial,
+                                                       unsigned *fault) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(sizeof(float2), pd, 2, rev_extra_bytes(pd.lut_count), sizeof(float4),
                                    sizeof(float4) << R_MAX_ROT);
@@ -1594,10 +1601,10 @@ __global__ void __launch_bounds__(NT, 2) k_reverse_blk(float *psi, float *lam, i
       bulk_g2s(tl + (h << pd.C), reinterpret_cast<const float2 *>(lam) + gi, bytes, &bar);
     }
     tile_codes(st, ng, t);
-    const bool ok = mbar_wait(&bar, parity);
+    const bool ok = mbar_wait(&bar, parity, fault);
     parity ^= 1u;
     if (__syncthreads_or(!ok)) {
-      mbar_wait(&bar, parity ^ 1u);   // a second bounded wait for the copies in flight
+      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
       break;
     }
     for (int b = nb - 1; b >= 0; --b) {
@@ -1744,26 +1751,66 @@ PassDesc worst_pass(int T, int C) {
 // Probe of the bounded wait: an mbarrier that nothing completes (one pending
 // arrival, no copies), waited on with `polls` polls; the wait gives up and
 // records itself exactly like a tile-copy wait that never completes.
-__global__ void k_wait_probe(uint32_t polls) {
+__global__ void k_wait_probe(uint32_t polls, unsigned *fault) {
   __shared__ uint64_t bar;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
-  if (threadIdx.x == 0) mbar_wait(&bar, 0, polls);
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, fault, polls);
 }
 
-cudaError_t launch_wait_probe(uint32_t polls, cudaStream_t st) {
-  k_wait_probe<<<1, 32, 0, st>>>(polls);
+cudaError_t launch_wait_probe(uint32_t polls, unsigned *fault, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(polls, fault);
   return cudaGetLastError();
 }
 
-cudaError_t read_wait_timeouts_async(unsigned *host, cudaStream_t st) {
-  return cudaMemcpyFromSymbolAsync(host, g_wait_timeouts, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);
+// Give-ups of the asynchronous calls on the current device: read, then cleared
+// (stream-ordered on st; the caller synchronizes st before using *host).
+cudaError_t take_async_faults(unsigned *host, cudaStream_t st) {
+  static const unsigned zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(host, g_async_faults, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(g_async_faults, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
+  return e;
 }
 
-cudaError_t clear_wait_timeouts(cudaStream_t st) {
-  static const unsigned zero = 0;
-  cudaError_t e = cudaMemcpyToSymbolAsync(g_wait_timeouts, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
-  return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+// FP64 FMA throughput probe: each thread runs 8 independent chains of `iters`
+// fused multiply-adds (2 flops each) on values that stay finite (|a| < 1).
+__global__ void __launch_bounds__(NT) k_fp64_rate(int iters, double seed, double *sink) {
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = seed * (double)(threadIdx.x + k + 1) * 1e-6;
+  const double a = 0.999999, b = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, b);
+  }
+  double t = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += v[k];
+  if (t == 12345.0) sink[0] = t;   // keeps the chains live; never true for these values
+}
+
+cudaError_t measure_fp64_rate(double *flops_per_s, cudaStream_t st) {
+  const int blocks = sm_count() * 2, iters = 1 << 11;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  k_fp64_rate<<<blocks, NT, 0, st>>>(16, 0.5, nullptr);   // warm-up
+  cudaEventRecord(e0, st);
+  k_fp64_rate<<<blocks, NT, 0, st>>>(iters, 0.5, nullptr);
+  cudaEventRecord(e1, st);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) *flops_per_s = (double)blocks * NT * iters * 8 * 2 / (ms * 1e-3);
+  return e;
 }
 
 size_t tile_smem_bytes(int amp_bytes, int T, int C, int vectors) {
@@ -1798,7 +1845,7 @@ cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st) {
 
 template <typename R>
 cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                         const BlockDesc *blocks, const void *lut, cudaStream_t st) {
+                         const BlockDesc *blocks, const void *lut, unsigned *fault, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const int nvec = 1;
   const int eb = (int)sizeof(typename SweepLut<R>::E);
@@ -1807,7 +1854,7 @@ cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *gro
   cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, 0, eb, (size_t)eb << R_MAX_ROT));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
-  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut));
+  k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), fault);
   return cudaGetLastError();
 }
 
@@ -1824,7 +1871,7 @@ int expect_grid(int n, int T, int C) {
 template <typename R>
 cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
                           const BlockDesc *blocks, const void *lut, double *partial, int grid, bool first,
-                          cudaStream_t st) {
+                          unsigned *fault, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const int nvec = 1;
   const size_t smem =
@@ -1834,7 +1881,7 @@ cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDe
                                         sizeof(C2) << R_MAX));
   if (e != cudaSuccess) return e;
   k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), partial,
-                            first ? 1 : 0);
+                            first ? 1 : 0, fault);
   return cudaGetLastError();
 }
 
@@ -1845,7 +1892,8 @@ cudaError_t launch_reduce_pairs(const double *partial, int nblocks, double *out,
 
 template <typename R>
 cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
-                          const BlockDesc *blocks, const void *lut, bool first, cudaStream_t st) {
+                          const BlockDesc *blocks, const void *lut, bool first, unsigned *fault,
+                          cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   if (blocks && pd.T >= 9 && pd.T <= T_LIMIT) {   // register-blocked path
     const size_t al = sizeof(C2) << R_MAX;
@@ -1861,7 +1909,8 @@ cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const
     cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0, sizeof(C2), al));
     if (e != cudaSuccess) return e;
     const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), first ? 1 : 0);
+    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), first ? 1 : 0,
+                              fault);
     return cudaGetLastError();
   }
   PassDesc pq = pd;
@@ -1892,7 +1941,7 @@ cudaError_t launch_dot(const R *psi, const R *lam, int n, double *partial, int g
 template <typename R>
 cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
                            const BlockDesc *blocks, bool one_param, const void *lut, const uint64_t *signmask,
-                           const R *wlut, double *partial, double *gphi, cudaStream_t st) {
+                           const R *wlut, double *partial, double *gphi, unsigned *fault, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   if constexpr (sizeof(R) == 4) {
     if (one_param && pd.T >= 9 && pd.T <= T_LIMIT) {   // register-blocked path (complex64)
@@ -1910,7 +1959,7 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
       if (e != cudaSuccess) return e;
       const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
       k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const float2 *>(lut), wlut,
-                                partial);
+                                partial, fault);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       const int nrot = pd.rot_end - pd.rot_begin;
       k_reduce_rot<<<(nrot + 127) / 128, 128, 0, st>>>(partial, (int)grid, nrot, gphi + pd.rot_begin);
@@ -1935,18 +1984,19 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
 #define Q2_INST(R)                                                                                  \
   template cudaError_t launch_init_hf<R>(R *, int, int, cudaStream_t);                             \
   template cudaError_t launch_sweep<R>(R *, int, const PassDesc &, const GroupDesc *,              \
-                                       const BlockDesc *, const void *, cudaStream_t);              \
+                                       const BlockDesc *, const void *, unsigned *, cudaStream_t);  \
   template int expect_grid<R>(int, int, int);                                                       \
   template cudaError_t launch_expect<R>(const R *, int, const PassDesc &, const GroupDesc *,        \
                                         const BlockDesc *, const void *, double *, int, bool,       \
-                                        cudaStream_t);                                              \
+                                        unsigned *, cudaStream_t);                                  \
   template cudaError_t launch_happly<R>(const R *, R *, int, const PassDesc &, const GroupDesc *,   \
-                                        const BlockDesc *, const void *, bool, cudaStream_t);       \
+                                        const BlockDesc *, const void *, bool, unsigned *,          \
+                                        cudaStream_t);                                              \
   template int dot_grid<R>(int);                                                                    \
   template cudaError_t launch_dot<R>(const R *, const R *, int, double *, int, cudaStream_t);       \
   template cudaError_t launch_reverse<R>(R *, R *, int, const PassDesc &, const GroupDesc *,        \
                                          const BlockDesc *, bool, const void *, const uint64_t *,   \
-                                         const R *, double *, double *, cudaStream_t);
+                                         const R *, double *, double *, unsigned *, cudaStream_t);
 
 Q2_INST(float)
 Q2_INST(double)

@@ -1,15 +1,19 @@
 // q2_expectation_noalloc: the energy of q2_expectation without device allocation.
 //
 // The scratch that q2_expectation takes from stream-ordered temporary memory
-// (per-CTA partial sums and the two result slots) and the Hamiltonian's
-// device tables (group and block descriptors, LUT) live here in one
-// file-scope static device array of Q2_NOALLOC_SCRATCH_BYTES.  Host code
-// only ever uses the array's device address, looked up once per device with
-// cudaGetSymbolAddress on the first call made with that device current.
+// (per-CTA partial sums, the two result slots and the call's fault word) and
+// the Hamiltonian's device tables (group and block descriptors, LUT) live
+// here in one file-scope static device array of Q2_NOALLOC_SCRATCH_BYTES.
+// Host code only ever uses the array's device address, which
+// cudaGetSymbolAddress gives for the current device; it is looked up once per
+// CUDA context (the first call on each device, and again if that device's
+// context is destroyed and created anew, since the module and its array are
+// then loaded at a new address).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -30,24 +34,57 @@ static __device__ __align__(256) unsigned char q2_noalloc_scratch[Q2_NOALLOC_SCR
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {nullptr};
+// Driver calls that name the calling thread's current context, reached through
+// the runtime so that the library needs no link against the driver library.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
 
-// Device address of the scratch array on the current device (looked up once per device).
+std::mutex g_mu;
+std::map<unsigned long long, void *> g_addr;   // context id -> device address of the scratch
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// Unique id of the current context (ids are never reused within a process); false if unknown.
+bool current_context_id(unsigned long long *id) {
+  if (!g_ctx_fns_tried) {
+    g_ctx_fns_tried = true;
+    cudaDriverEntryPointQueryResult q1, q2r;
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2r) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2r == cudaDriverEntryPointSuccess) {
+      g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+  }
+  if (!g_ctx_current || !g_ctx_id) return false;
+  void *ctx = nullptr;
+  if (g_ctx_current(&ctx) != 0 || !ctx) return false;
+  return g_ctx_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current context.
 q2_status scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaSetDevice(dev);   // makes the device's primary context current
   if (e != cudaSuccess) return set_error(Q2_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(Q2_ERR_UNSUPPORTED, "device index too large");
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, q2_noalloc_scratch);
-    if (e != cudaSuccess || !p) return set_error(Q2_ERR_CUDA, "cudaGetSymbolAddress failed for the no-allocation scratch");
-    g_addr[dev] = p;
+  unsigned long long id = 0;
+  const bool keyed = current_context_id(&id);
+  if (keyed) {
+    auto it = g_addr.find(id);
+    if (it != g_addr.end()) {
+      *out = it->second;
+      return Q2_OK;
+    }
   }
-  *out = g_addr[dev];
+  void *p = nullptr;
+  e = cudaGetSymbolAddress(&p, q2_noalloc_scratch);
+  if (e != cudaSuccess || !p) return set_error(Q2_ERR_CUDA, "cudaGetSymbolAddress failed for the no-allocation scratch");
+  if (keyed) g_addr[id] = p;   // without a context id the address is looked up on every call
+  *out = p;
   return Q2_OK;
 }
 
@@ -55,9 +92,9 @@ size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 template <typename R>
 cudaError_t run(const R *psi, int n, const HamPlan &h, const GroupDesc *groups, const BlockDesc *blocks,
-                const void *lut, double *partial, int grid, double *out, cudaStream_t st) {
+                const void *lut, double *partial, int grid, double *out, unsigned *fault, cudaStream_t st) {
   for (size_t i = 0; i < h.passes.size(); ++i) {
-    cudaError_t e = launch_expect<R>(psi, n, h.passes[i], groups, blocks, lut, partial, grid, i == 0, st);
+    cudaError_t e = launch_expect<R>(psi, n, h.passes[i], groups, blocks, lut, partial, grid, i == 0, fault, st);
     if (e != cudaSuccess) return e;
   }
   return launch_reduce_pairs(partial, grid, out, st);
@@ -80,7 +117,7 @@ extern "C" q2_status q2_expectation_noalloc(const void *psi_dev, int n, q2_dtype
   const int amp = dtype == Q2_C64 ? 8 : 16;
   const int C = std::min(chunk, hp->T);
   const int grid = dtype == Q2_C64 ? expect_grid<float>(n, hp->T, C) : expect_grid<double>(n, hp->T, C);
-  // scratch layout: [out 2][partials 2*grid][groups][blocks][lut]
+  // scratch layout: [out 2][fault word][partials 2*grid][groups][blocks][lut]
   const size_t o_part = 256;
   const size_t o_groups = o_part + up256(sizeof(double) * 2 * (size_t)grid);
   const size_t o_blocks = o_groups + up256(sizeof(GroupDesc) * hp->groups.size());
@@ -103,32 +140,34 @@ extern "C" q2_status q2_expectation_noalloc(const void *psi_dev, int n, q2_dtype
     for (size_t i = 0; i < lutf.size(); ++i) lutf[i] = (float)hp->lut2[i];
     lut_src = lutf.data();
   }
-  cudaError_t e = cudaMemcpyAsync(base + o_groups, hp->groups.data(), sizeof(GroupDesc) * hp->groups.size(),
-                                  cudaMemcpyHostToDevice, st);
+  double *out = reinterpret_cast<double *>(base);
+  unsigned *fault = reinterpret_cast<unsigned *>(base + 2 * sizeof(double));
+  cudaError_t e = cudaMemsetAsync(base, 0, 2 * sizeof(double) + sizeof(unsigned), st);   // sums and fault word
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + o_groups, hp->groups.data(), sizeof(GroupDesc) * hp->groups.size(),
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !hp->blocks.empty())
     e = cudaMemcpyAsync(base + o_blocks, hp->blocks.data(), sizeof(BlockDesc) * hp->blocks.size(),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && hp->lut_entries > 0)
     e = cudaMemcpyAsync(base + o_lut, lut_src, (size_t)amp * (size_t)hp->lut_entries, cudaMemcpyHostToDevice, st);
-  double *out = reinterpret_cast<double *>(base);
   double *partial = reinterpret_cast<double *>(base + o_part);
   const GroupDesc *groups = reinterpret_cast<const GroupDesc *>(base + o_groups);
   const BlockDesc *blocks = reinterpret_cast<const BlockDesc *>(base + o_blocks);
   if (e == cudaSuccess)
     e = dtype == Q2_C64
-            ? run<float>(static_cast<const float *>(psi_dev), n, *hp, groups, blocks, base + o_lut, partial, grid, out, st)
+            ? run<float>(static_cast<const float *>(psi_dev), n, *hp, groups, blocks, base + o_lut, partial, grid, out,
+                         fault, st)
             : run<double>(static_cast<const double *>(psi_dev), n, *hp, groups, blocks, base + o_lut, partial, grid, out,
-                          st);
+                          fault, st);
   double host_out[2] = {0.0, 0.0};
   unsigned waits = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, out, sizeof(host_out), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = read_wait_timeouts_async(&waits, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&waits, fault, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  const cudaError_t es = cudaStreamSynchronize(st);   // always: the host buffers above must outlive the copies
+  if (e == cudaSuccess) e = es;
   if (e != cudaSuccess) return set_error(Q2_ERR_CUDA, cudaGetErrorString(e));
-  if (waits) {
-    clear_wait_timeouts(st);
-    return set_error(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
-  }
+  if (waits) return set_error(Q2_ERR_TIMEOUT, "a device wait for a tile copy timed out");
   *energy_out = host_out[0] / host_out[1];
   if (norm_out) *norm_out = host_out[1];
   return Q2_OK;

@@ -3,8 +3,10 @@
 Requests are (Hamiltonian, ansatz, theta, want_grad) solves on 10..26 qubits.
 The loop keeps every problem's Pauli tables resident on the device (one
 library handle pair per distinct problem), admits requests by device-memory
-footprint through the C++ admission core (include/q2_serve.h), and runs them
-while others are still on the GPU:
+footprint through the C++ admission core (include/q2_serve.h) -- running
+workspaces plus the resident tables, with unused problems released least
+recently used first when room is needed -- and runs them while others are
+still on the GPU:
 
 * small states (n <= 12) are gathered for a short window and evaluated
   together in one persistent launch (q2_batch_energy_grad), each CTA holding
@@ -82,12 +84,14 @@ def _setup_core():
     P, I, I64, D, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
     L.q2_server_create.argtypes = [SZ, I, D, ctypes.POINTER(P)]
     L.q2_server_destroy.argtypes = [P]
-    L.q2_server_submit.argtypes = [P, I64, SZ, D]
+    L.q2_server_submit.argtypes = [P, I64, SZ, I64, SZ, D]
     L.q2_server_admit.argtypes = [P, D, ctypes.POINTER(I64), I]
     L.q2_server_admit.restype = I
     L.q2_server_expire.argtypes = [P, D, ctypes.POINTER(I64), I]
     L.q2_server_expire.restype = I
     L.q2_server_complete.argtypes = [P, I64, D]
+    L.q2_server_take_evicted.argtypes = [P, ctypes.POINTER(I64), I]
+    L.q2_server_take_evicted.restype = I
     L.q2_server_stats.argtypes = [P, ctypes.POINTER(D)]
     return L
 
@@ -100,8 +104,7 @@ class Server:
         import torch
         self._torch = torch
         self.dtype = dtype
-        dev = torch.device(device)
-        self.device = dev.index if dev.index is not None else torch.cuda.current_device()
+        self.device = self._device_index(device)
         self.budget = int(budget_bytes)
         self.batch_window_s = batch_window_s
         self.max_batch = max_batch
@@ -115,8 +118,11 @@ class Server:
         self._lock = threading.Lock()
         self._wake = threading.Condition(self._lock)
         self._jobs = {}
-        self._tables = {}
+        self._tables = {}          # problem key -> (Ansatz, Hamiltonian) handles
+        self._table_ids = {}       # problem key -> int64 id in the admission core
+        self._table_keys = {}      # id -> problem key
         self._table_lock = threading.Lock()
+        self._closed = False
         self._large = queue.Queue()
         self._small = []
         self._small_cv = threading.Condition()
@@ -132,24 +138,33 @@ class Server:
     def now(self):
         return time.perf_counter() - self._t0
 
-    def footprint(self, problem, want_grad):
+    def footprint(self, problem, want_grad, handles=None):
         """Device bytes a request needs while it runs (state vectors and per-call tables)."""
-        a, _ = self._handles(problem)
+        a, h = handles if handles else self._handles(problem)
         if problem.n <= SMALL_MAX_QUBITS:
             A = (ctypes.c_void_p * 1)(a.handle)
-            H = (ctypes.c_void_p * 1)(self._handles(problem)[1].handle)
+            H = (ctypes.c_void_p * 1)(h.handle)
             return int(lib().q2_batch_workspace_bytes(1, A, H, _dtype_code(self.dtype)))
         return int(a.workspace_bytes(self.dtype, want_grad))
+
+    def table_bytes(self, handles):
+        """Device bytes of a problem's resident tables (Hamiltonian and ansatz handles)."""
+        a, h = handles
+        return int(a.table_bytes(self.dtype)[0] + h.table_bytes(self.dtype))
 
     def submit(self, rid, problem, theta, want_grad):
         """Queue one request; returns a Future resolving to a Result."""
         fut = Future()
         job = _Job(int(rid), problem, np.asarray(theta, dtype=np.float64), bool(want_grad), fut, self.now())
         job.handles = self._handles(problem)
-        nbytes = self.footprint(problem, want_grad)
+        nbytes = self.footprint(problem, want_grad, job.handles)
+        tbytes = self.table_bytes(job.handles)
+        pid = self._table_ids[problem.key]
         with self._lock:
+            if self._closed:
+                raise RuntimeError("server is closed")
             self._jobs[job.rid] = job
-            st = self._L.q2_server_submit(self._core, job.rid, nbytes, job.t_submit)
+            st = self._L.q2_server_submit(self._core, job.rid, nbytes, pid, tbytes, job.t_submit)
             if st != Q2_OK:
                 del self._jobs[job.rid]
                 fut.set_result(Result(job.rid, st, t_submit=job.t_submit, t_done=self.now()))
@@ -158,24 +173,43 @@ class Server:
         return fut
 
     def stats(self):
-        out = (ctypes.c_double * 11)()
+        out = (ctypes.c_double * 14)()
         self._L.q2_server_stats(self._core, out)
         keys = ["submitted", "admitted", "completed", "expired", "queued", "running", "bytes_in_use",
-                "high_water_bytes", "p50_s", "p99_s", "mean_s"]
+                "high_water_bytes", "p50_s", "p99_s", "mean_s", "table_bytes", "resident_problems",
+                "evictions"]
         return dict(zip(keys, list(out)))
 
-    def close(self):
+    def close(self, timeout_s=600.0):
+        """Stop the loops and release the admission core and the resident tables.
+
+        Waits for every worker to return (each is at most inside one library call,
+        whose device waits are bounded).  If one is still alive after timeout_s the
+        core and the tables are kept (a worker may still use them) and RuntimeError
+        is raised."""
         with self._lock:
+            if self._closed:
+                return
             self._stop = True
             self._wake.notify_all()
         with self._small_cv:
             self._small_cv.notify_all()
         for _ in self._threads:
             self._large.put(None)
+        deadline = time.perf_counter() + timeout_s
         for t in self._threads:
-            t.join(timeout=30)
+            t.join(timeout=max(0.0, deadline - time.perf_counter()))
+        alive = [t for t in self._threads if t.is_alive()]
+        if alive:
+            raise RuntimeError(f"{len(alive)} serving threads still running after {timeout_s} s; "
+                               "the admission core and the resident tables are kept")
+        self._fail_all(Q2_ERR_INVALID, "server closed before the request ran")
+        with self._lock:
+            self._closed = True
         self._L.q2_server_destroy(self._core)
         self._core = None
+        with self._table_lock:
+            self._tables.clear()
 
     # ------------------------------------------------------------------ resident tables
 
@@ -187,7 +221,23 @@ class Server:
                             problem.rot_coef, problem.n_params),
                      Hamiltonian(problem.n, problem.ham_x, problem.ham_z, problem.ham_c))
                 self._tables[problem.key] = h
+            if problem.key not in self._table_ids:
+                pid = len(self._table_ids) + 1
+                self._table_ids[problem.key] = pid
+                self._table_keys[pid] = problem.key
             return h
+
+    def _release_evicted(self):
+        """Drop the handles of problems the core released.  A request that already holds
+        them keeps them alive until it finishes; the next request re-creates them."""
+        ids = (ctypes.c_int64 * 64)()
+        while True:
+            k = self._L.q2_server_take_evicted(self._core, ids, 64)
+            if k <= 0:
+                return
+            with self._table_lock:
+                for i in range(k):
+                    self._tables.pop(self._table_keys.get(ids[i]), None)
 
     # ------------------------------------------------------------------ loops
 
@@ -213,6 +263,7 @@ class Server:
                 admitted = [self._jobs[ids[i]] for i in range(max(k, 0))]
                 if not expired and not admitted:
                     self._wake.wait(timeout=0.002)
+            self._release_evicted()
             for job in expired:
                 if not job.future.done():
                     job.future.set_result(Result(job.rid, Q2_ERR_TIMEOUT, t_submit=job.t_submit, t_done=self.now()))
@@ -247,10 +298,32 @@ class Server:
             self._fail_all(Q2_ERR_INVALID, "stream worker: " + repr(exc))
             raise
 
+    # ------------------------------------------------------------------ device work (overridable)
+
+    def _device_index(self, device):
+        dev = self._torch.device(device)
+        return dev.index if dev.index is not None else self._torch.cuda.current_device()
+
+    def _make_stream(self):
+        """A CUDA stream of this loop's device, made current for the calling thread's device."""
+        self._torch.cuda.set_device(self.device)
+        return self._torch.cuda.Stream(device=self.device)
+
+    def _run_batch(self, batch, stream, ws):
+        with self._torch.cuda.stream(stream):
+            return batch_energy_grad([j.handles[0] for j in batch], [j.handles[1] for j in batch],
+                                     [j.theta for j in batch], [j.want_grad for j in batch],
+                                     dtype=self.dtype, workspace=ws)
+
+    def _run_large(self, job, stream, ws):
+        with self._torch.cuda.stream(stream):
+            return vqe_energy_grad(job.handles[0], job.handles[1], job.theta, dtype=self.dtype,
+                                   want_grad=job.want_grad, workspace=ws)
+
+    # ------------------------------------------------------------------ loop bodies
+
     def _batch_loop_body(self):
-        torch = self._torch
-        torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(device=self.device)
+        stream = self._make_stream()
         ws = None
         while True:
             with self._small_cv:
@@ -262,10 +335,7 @@ class Server:
             with self._small_cv:
                 batch, self._small = self._small[:self.max_batch], self._small[self.max_batch:]
             try:
-                with torch.cuda.stream(stream):
-                    e, g, ws = batch_energy_grad([j.handles[0] for j in batch], [j.handles[1] for j in batch],
-                                                 [j.theta for j in batch], [j.want_grad for j in batch],
-                                                 dtype=self.dtype, workspace=ws)
+                e, g, ws = self._run_batch(batch, stream, ws)
                 for j, ej, gj in zip(batch, e, g):
                     self._finish(j, Q2_OK, float(ej), gj, "batch")
             except Q2Error as exc:
@@ -277,18 +347,14 @@ class Server:
                 raise
 
     def _worker_loop_body(self):
-        torch = self._torch
-        torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(device=self.device)
+        stream = self._make_stream()
         ws = None
         while True:
             job = self._large.get()
             if job is None:
                 return
             try:
-                with torch.cuda.stream(stream):
-                    e, g, ws = vqe_energy_grad(job.handles[0], job.handles[1], job.theta, dtype=self.dtype,
-                                               want_grad=job.want_grad, workspace=ws)
+                e, g, ws = self._run_large(job, stream, ws)
                 self._finish(job, Q2_OK, e, g, "stream")
             except Q2Error as exc:
                 self._finish(job, exc.status, path="stream", error=str(exc))
