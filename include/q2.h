@@ -116,6 +116,36 @@ q2_status q2_ham_destroy(q2_ham *ham);
  */
 q2_status q2_async_status(void *stream);
 
+/*
+ * Term-group parallelism (Sec. "Parallel evaluation of an expectation value",
+ * Fig. 4: the Pauli strings are split over processes and the partial
+ * energies are summed).  q2_ham_shard creates a handle for shard `shard` of
+ * `n_shards` of `ham`: it holds a copy of all terms but evaluates only its
+ * share of the xmask-group passes of ham's full schedule (for each dtype the
+ * schedule is built as for ham, and its passes are dealt to the shards
+ * largest first -- work = pair evaluations per amplitude plus one state
+ * read -- each to the least loaded shard).  The shards of one Hamiltonian
+ * partition its terms, so with the same psi (or ansatz and theta) the
+ * energies of q2_expectation / q2_vqe_energy_grad on the shards, and their
+ * gradients, sum to those of ham (each shard's energy is its share of
+ * <psi|H|psi> divided by the full <psi|psi>); the gradient of a shard is that
+ * of its share of <psi|H|psi>.  A shard may get no pass (more shards than
+ * passes): its energy and gradient are then 0.  A shard cannot be sharded
+ * again and is not accepted by q2_batch_energy_grad (Q2_ERR_UNSUPPORTED).
+ * `n_shards` >= 1, 0 <= shard < n_shards.  *out is owned by the caller
+ * (q2_ham_destroy).
+ */
+q2_status q2_ham_shard(const q2_ham *ham, int shard, int n_shards, q2_ham **out);
+
+/*
+ * Indices (into the term arrays given to q2_ham_create, ascending) of the
+ * terms a handle evaluates for `dtype`: all terms for a whole Hamiltonian,
+ * the shard's terms for a shard.  With idx_out = NULL only *count is set;
+ * otherwise *count must hold idx_out's capacity on entry and receives the
+ * number written.  Host only.
+ */
+q2_status q2_ham_shard_terms(const q2_ham *ham, q2_dtype dtype, int64_t *idx_out, int64_t *count);
+
 /* Number of terms and of distinct xmask groups of a Hamiltonian handle. */
 q2_status q2_ham_info(const q2_ham *ham, int64_t *n_terms, int64_t *n_groups);
 

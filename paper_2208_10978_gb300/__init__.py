@@ -63,6 +63,8 @@ _SIGS = {
     "q2_expectation_noalloc": ([_P, _I, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P], _I),
     "q2_pool_gradients": ([_P, _P, _P, _I, _I64, _P, _P, ctypes.POINTER(_D), _P, _P, _SZ, _P], _I),
     "q2_async_status": ([_P], _I),
+    "q2_ham_shard": ([_P, _I, _I, ctypes.POINTER(_P)], _I),
+    "q2_ham_shard_terms": ([_P, _I, _P, ctypes.POINTER(_I64)], _I),
     "q2_ham_table_bytes": ([_P, _I, ctypes.POINTER(_SZ)], _I),
     "q2_ansatz_table_bytes": ([_P, _I, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)], _I),
 }
@@ -191,6 +193,25 @@ class Hamiltonian:
         _check(lib().q2_expectation(p, self.n, d, self._h, ctypes.byref(e), ctypes.byref(nrm),
                                     _stream_ptr()))
         return e.value, nrm.value
+
+    def shard(self, shard, n_shards):
+        """Shard `shard` of `n_shards` of this Hamiltonian (q2_ham_shard): a handle that evaluates
+        only its share of the xmask-group passes; the shards' energies and gradients sum to this
+        Hamiltonian's."""
+        h = _P()
+        _check(lib().q2_ham_shard(self._h, int(shard), int(n_shards), ctypes.byref(h)))
+        out = Hamiltonian.__new__(Hamiltonian)
+        out.n = self.n
+        out._h = h
+        return out
+
+    def shard_terms(self, dtype="complex64"):
+        """Indices of the terms this handle evaluates for a state dtype (ascending)."""
+        cnt = _I64(0)
+        _check(lib().q2_ham_shard_terms(self._h, _dtype_code(dtype), None, ctypes.byref(cnt)))
+        idx = np.zeros(max(1, cnt.value), dtype=np.int64)
+        _check(lib().q2_ham_shard_terms(self._h, _dtype_code(dtype), _np_ptr(idx), ctypes.byref(cnt)))
+        return idx[:cnt.value]
 
     def table_bytes(self, dtype="complex64"):
         """Device bytes of this Hamiltonian's resident tables for a state dtype."""

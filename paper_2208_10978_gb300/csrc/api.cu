@@ -153,6 +153,7 @@ struct q2_ham {
   std::vector<uint64_t> x, z;
   std::vector<double> c;
   int64_t n_groups = 0;
+  int shard = 0, n_shards = 1;   // a shard evaluates only its share of the passes of the full plan
   HamPlan plan[2];
   bool planned[2] = {false, false};
   DevTables dev[2];
@@ -185,18 +186,26 @@ struct q2_ansatz {
 
 namespace {
 
+// Host schedule of a Hamiltonian for a dtype (the caller holds h->mu); a shard keeps
+// only its passes of the full schedule.
+q2_status plan_ham_locked(q2_ham *h, q2_dtype d) {
+  if (h->planned[d]) return Q2_OK;
+  try {
+    h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
+                                ham_tile_bits(d), g_chunk[d]);
+    restrict_to_shard(h->plan[d], h->shard, h->n_shards);
+  } catch (const std::exception &e) {
+    return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
+  }
+  h->planned[d] = true;
+  return Q2_OK;
+}
+
 q2_status ham_tables(const q2_ham *hc, q2_dtype d, const HamPlan **plan, const DevTables **dev) {
   q2_ham *h = const_cast<q2_ham *>(hc);
   std::lock_guard<std::mutex> g(h->mu);
-  if (!h->planned[d]) {
-    try {
-      h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
-                                  ham_tile_bits(d), g_chunk[d]);
-    } catch (const std::exception &e) {
-      return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
-    }
-    h->planned[d] = true;
-  }
+  q2_status ps = plan_ham_locked(h, d);
+  if (ps != Q2_OK) return ps;
   DevTables &t = h->dev[d];
   int device = 0;
   Q2_CUDA(cudaGetDevice(&device), "cudaGetDevice");
@@ -296,6 +305,13 @@ cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups,
 template <typename R>
 cudaError_t run_expect(const R *psi, int n, const HamPlan &h, const DevTables &t, double *partial,
                        int grid, double *out2, unsigned *fault, cudaStream_t st) {
+  if (h.passes.empty()) {   // no terms (or a shard without passes): energy 0, norm by a dot product
+    const int dg = dot_grid<R>(n);
+    cudaError_t e = launch_dot<R>(psi, psi, n, partial, dg, st);
+    if (e == cudaSuccess) e = launch_reduce_pairs(partial, dg, out2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out2, 0, sizeof(double), st);
+    return e;
+  }
   for (size_t i = 0; i < h.passes.size(); ++i) {
     cudaError_t e =
         launch_expect<R>(psi, n, h.passes[i], t.groups, t.blocks, t.lut, partial, grid, i == 0, fault, st);
@@ -307,6 +323,7 @@ cudaError_t run_expect(const R *psi, int n, const HamPlan &h, const DevTables &t
 template <typename R>
 cudaError_t run_happly(const R *psi, R *lam, int n, const HamPlan &h, const DevTables &t, unsigned *fault,
                        cudaStream_t st) {
+  if (h.passes.empty()) return cudaMemsetAsync(lam, 0, (2 * sizeof(R)) << n, st);   // H = 0 here
   for (size_t i = 0; i < h.passes.size(); ++i) {
     cudaError_t e = launch_happly<R>(psi, lam, n, h.passes[i], t.groups, t.blocks, t.lut, i == 0, fault, st);
     if (e != cudaSuccess) return e;
@@ -663,6 +680,44 @@ q2_status q2_async_status(void *stream) {
   return Q2_OK;
 }
 
+q2_status q2_ham_shard(const q2_ham *ham, int shard, int n_shards, q2_ham **out) {
+  if (!ham || !out) return fail(Q2_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (ham->n_shards != 1) return fail(Q2_ERR_INVALID, "a shard cannot be sharded again");
+  if (n_shards < 1 || shard < 0 || shard >= n_shards) return fail(Q2_ERR_INVALID, "shard index out of range");
+  q2_ham *h = new (std::nothrow) q2_ham;
+  if (!h) return fail(Q2_ERR_OOM, "host allocation");
+  h->n = ham->n;
+  h->x = ham->x;
+  h->z = ham->z;
+  h->c = ham->c;
+  h->n_groups = ham->n_groups;
+  h->shard = shard;
+  h->n_shards = n_shards;
+  *out = h;
+  return Q2_OK;
+}
+
+q2_status q2_ham_shard_terms(const q2_ham *ham, q2_dtype dtype, int64_t *idx_out, int64_t *count) {
+  if (!ham || !count) return fail(Q2_ERR_INVALID, "NULL argument");
+  if (!valid_dtype(dtype)) return fail(Q2_ERR_INVALID, "unknown dtype");
+  const HamPlan *hp;
+  int chunk = 0;
+  q2_status s = ham_host_plan(ham, dtype, &hp, &chunk);
+  if (s != Q2_OK) return s;
+  std::vector<int64_t> idx;
+  for (const PassDesc &pd : hp->passes)
+    for (int g = pd.g_begin; g < pd.g_end; ++g)
+      idx.insert(idx.end(), hp->term_idx.begin() + hp->term_begin[g], hp->term_idx.begin() + hp->term_begin[g + 1]);
+  std::sort(idx.begin(), idx.end());
+  if (idx_out) {
+    if (*count < (int64_t)idx.size()) return fail(Q2_ERR_INVALID, "term index buffer too small");
+    std::copy(idx.begin(), idx.end(), idx_out);
+  }
+  *count = (int64_t)idx.size();
+  return Q2_OK;
+}
+
 q2_status q2_ham_info(const q2_ham *ham, int64_t *n_terms, int64_t *n_groups) {
   if (!ham) return fail(Q2_ERR_INVALID, "NULL handle");
   if (n_terms) *n_terms = (int64_t)ham->c.size();
@@ -683,10 +738,11 @@ q2_status q2_expectation(const void *psi_dev, int n, q2_dtype dtype, const q2_ha
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int C = std::min(g_chunk[dtype], hp->T);
   const int grid = dtype == Q2_C64 ? expect_grid<float>(n, hp->T, C) : expect_grid<double>(n, hp->T, C);
-  // [partials 2 * grid][result block of 4 doubles: sums, fault word]
+  const int slots = std::max(grid, dtype == Q2_C64 ? dot_grid<float>(n) : dot_grid<double>(n));
+  // [partials 2 * slots][result block of 4 doubles: sums, fault word]
   double *tmp = nullptr;
-  Q2_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * (2 * (size_t)grid + 4), st), "cudaMallocAsync(partials)");
-  double *out4 = tmp + 2 * grid;
+  Q2_CUDA(cudaMallocAsync((void **)&tmp, sizeof(double) * (2 * (size_t)slots + 4), st), "cudaMallocAsync(partials)");
+  double *out4 = tmp + 2 * slots;
   double host_out[4] = {0, 0, 0, 0};
   cudaError_t e = cudaMemsetAsync(out4, 0, sizeof(double) * 4, st);
   if (e == cudaSuccess)
@@ -961,6 +1017,7 @@ q2_status q2_batch_energy_grad(int n_requests, const q2_ansatz *const *ansatz, c
     if (!ansatz[b] || !ham[b] || !theta[b]) return fail(Q2_ERR_INVALID, "NULL request entry");
     if (ansatz[b]->n > SMALL_MAX_QUBITS) return fail(Q2_ERR_INVALID, "batched requests need n <= 12");
     if (ham[b]->n != ansatz[b]->n) return fail(Q2_ERR_INVALID, "Hamiltonian and ansatz qubit counts differ");
+    if (ham[b]->n_shards != 1) return fail(Q2_ERR_UNSUPPORTED, "the batched path takes whole Hamiltonians, not shards");
     q2_status s = check_finite(ansatz[b]->n_params, theta[b], "theta");
     if (s != Q2_OK) return s;
     if (want_grad[b] && (!grad_out || !grad_out[b])) return fail(Q2_ERR_INVALID, "NULL gradient output");
@@ -1182,15 +1239,8 @@ namespace q2 {
 q2_status ham_host_plan(const q2_ham *hc, q2_dtype d, const HamPlan **plan, int *chunk) {
   q2_ham *h = const_cast<q2_ham *>(hc);
   std::lock_guard<std::mutex> g(h->mu);
-  if (!h->planned[d]) {
-    try {
-      h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
-                                  ham_tile_bits(d), g_chunk[d]);
-    } catch (const std::exception &e) {
-      return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
-    }
-    h->planned[d] = true;
-  }
+  q2_status s = plan_ham_locked(h, d);
+  if (s != Q2_OK) return s;
   *plan = &h->plan[d];
   *chunk = g_chunk[d];
   return Q2_OK;

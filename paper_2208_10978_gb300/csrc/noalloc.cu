@@ -93,6 +93,13 @@ size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 template <typename R>
 cudaError_t run(const R *psi, int n, const HamPlan &h, const GroupDesc *groups, const BlockDesc *blocks,
                 const void *lut, double *partial, int grid, double *out, unsigned *fault, cudaStream_t st) {
+  if (h.passes.empty()) {   // no terms (or a shard without passes): energy 0, norm by a dot product
+    const int dg = dot_grid<R>(n);
+    cudaError_t e = launch_dot<R>(psi, psi, n, partial, dg, st);
+    if (e == cudaSuccess) e = launch_reduce_pairs(partial, dg, out, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(double), st);
+    return e;
+  }
   for (size_t i = 0; i < h.passes.size(); ++i) {
     cudaError_t e = launch_expect<R>(psi, n, h.passes[i], groups, blocks, lut, partial, grid, i == 0, fault, st);
     if (e != cudaSuccess) return e;
@@ -117,9 +124,10 @@ extern "C" q2_status q2_expectation_noalloc(const void *psi_dev, int n, q2_dtype
   const int amp = dtype == Q2_C64 ? 8 : 16;
   const int C = std::min(chunk, hp->T);
   const int grid = dtype == Q2_C64 ? expect_grid<float>(n, hp->T, C) : expect_grid<double>(n, hp->T, C);
-  // scratch layout: [out 2][fault word][partials 2*grid][groups][blocks][lut]
+  const int slots = std::max(grid, dtype == Q2_C64 ? dot_grid<float>(n) : dot_grid<double>(n));
+  // scratch layout: [out 2][fault word][partials 2*slots][groups][blocks][lut]
   const size_t o_part = 256;
-  const size_t o_groups = o_part + up256(sizeof(double) * 2 * (size_t)grid);
+  const size_t o_groups = o_part + up256(sizeof(double) * 2 * (size_t)slots);
   const size_t o_blocks = o_groups + up256(sizeof(GroupDesc) * hp->groups.size());
   const size_t o_lut = o_blocks + up256(sizeof(BlockDesc) * hp->blocks.size());
   const size_t total = o_lut + up256((size_t)amp * (size_t)hp->lut_entries);

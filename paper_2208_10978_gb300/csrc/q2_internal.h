@@ -157,7 +157,17 @@ struct HamPlan {
   std::vector<BlockDesc> blocks;
   std::vector<double> lut2;            // (R, Q) per group and code
   int64_t lut_entries = 0;
+  // Terms of each group: indices term_idx[term_begin[g] .. term_begin[g + 1]) of the
+  // Hamiltonian's term arrays (groups as stored, i.e. after block reordering).
+  std::vector<int64_t> term_idx;
+  std::vector<int64_t> term_begin;
 };
+
+// Keep only the passes that shard `shard` of `n_shards` evaluates: passes are
+// dealt to shards largest first (work = pair evaluations per amplitude, a
+// diagonal group counting twice, plus one for the state read), each to the
+// least loaded shard (ties: lower pass index, lower shard index).
+void restrict_to_shard(HamPlan &p, int shard, int n_shards);
 
 RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, int T, int C);
 void set_param_weights(RotPlan &p, const int32_t *param, const double *coef);

@@ -591,6 +591,7 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
 
   // 3. descriptors and LUT of combined coefficients (R, Q) per code
   uint32_t lut = 0;
+  std::vector<size_t> raw_of;   // raw group of each descriptor, in descriptor order
   for (size_t p = 0; p < pass_groups.size(); ++p) {
     const Tiling tl = make_tiling(n, T, C, pass_gens[p]);
     PassDesc pd = make_pass(tl);
@@ -598,6 +599,7 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
     pd.rot_begin = pd.rot_end = 0;
     lut = (uint32_t)align_up_int((int)lut, 1 << R_MAX);
     for (size_t g : pass_groups[p]) {
+      raw_of.push_back(g);
       const RawGroup &rg = groups[g];
       lut = (uint32_t)align_up_int((int)lut, 1 << rg.basis.rank());
       GroupDesc d = make_desc(rg, tl, lut);
@@ -629,12 +631,51 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
     pd.lut_begin = (int)H.groups[pd.g_begin].lut;
     pd.lut_count = (int)lut - pd.lut_begin;
     pd.b_begin = (int)H.blocks.size();
+    // block formation may reorder the pass's descriptors: carry each one's raw group along
+    // (the LUT offset identifies a descriptor uniquely within a pass)
+    std::vector<std::pair<uint32_t, size_t>> before;
+    for (int g = pd.g_begin; g < pd.g_end; ++g) before.push_back({H.groups[g].lut, raw_of[g]});
     form_blocks(H.groups, pd.g_begin, pd.g_end, T, block_dmax(T, D_MAX_EXPECT), true, H.blocks);
+    std::sort(before.begin(), before.end());
+    for (int g = pd.g_begin; g < pd.g_end; ++g) {
+      auto it = std::lower_bound(before.begin(), before.end(), std::make_pair(H.groups[g].lut, (size_t)0));
+      raw_of[g] = it->second;
+    }
     pd.b_end = (int)H.blocks.size();
     H.passes.push_back(pd);
   }
   H.lut_entries = lut;
+  H.term_begin.assign(1, 0);
+  for (size_t g = 0; g < H.groups.size(); ++g) {
+    const RawGroup &rg = groups[raw_of[g]];
+    H.term_idx.insert(H.term_idx.end(), rg.members.begin(), rg.members.end());
+    H.term_begin.push_back((int64_t)H.term_idx.size());
+  }
   return H;
+}
+
+void restrict_to_shard(HamPlan &p, int shard, int n_shards) {
+  if (n_shards <= 1) return;
+  const size_t np = p.passes.size();
+  std::vector<double> cost(np, 1.0);
+  for (size_t i = 0; i < np; ++i)
+    for (int g = p.passes[i].g_begin; g < p.passes[i].g_end; ++g) cost[i] += p.groups[g].kind == KIND_DIAG ? 2.0 : 1.0;
+  std::vector<size_t> order(np);
+  std::iota(order.begin(), order.end(), (size_t)0);
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+  std::vector<double> load(n_shards, 0.0);
+  std::vector<int> owner(np, 0);
+  for (size_t i : order) {
+    int best = 0;
+    for (int s = 1; s < n_shards; ++s)
+      if (load[s] < load[best]) best = s;
+    owner[i] = best;
+    load[best] += cost[i];
+  }
+  std::vector<PassDesc> keep;
+  for (size_t i = 0; i < np; ++i)
+    if (owner[i] == shard) keep.push_back(p.passes[i]);
+  p.passes.swap(keep);
 }
 
 }  // namespace q2

@@ -332,3 +332,42 @@ def test_timeout_reported_only_by_the_call_that_timed_out():
         assert not isinstance(e, Exception), e
         assert abs(e - e_ref) < TOL_E["complex64"]
     q2.async_status()          # the probe's give-ups are not the asynchronous calls' either
+
+
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+def test_hamiltonian_shards_sum_to_whole(dtype):
+    """Term-group sharding (q2_ham_shard) on one GPU: the shards' energies and gradients, each
+    evaluated through q2_vqe_energy_grad and q2_expectation, sum to the whole Hamiltonian's and
+    to the oracle's; with more shards than passes some shards are empty and give exactly 0."""
+    w = uccsd_energy(12, 6, seed=4)
+    a = w.ansatz
+    ans = q2.Ansatz.from_uccsd(a)
+    ham = q2.Hamiltonian(12, w.ham.x, w.ham.z, w.ham.c)
+    theta = np.random.default_rng(2).normal(0, 0.3, size=a.n_params)
+    e_ref, gphi = c_oracle.energy_and_gradient(12, 6, a.x, a.z, a.angles(theta), w.ham.x, w.ham.z, w.ham.c)
+    g_ref = sv.fold_to_theta(gphi, a.param, a.coef, a.n_params)
+    e_all, g_all, ws = q2.vqe_energy_grad(ans, ham, theta, dtype=dtype, want_grad=True)
+    psi = q2.new_state(12, dtype)
+    q2.state_init_hf(psi, 12, 6)
+    q2.apply_pauli_rotations(psi, 12, a.x, a.z, a.angles(theta))
+    e_psi, _ = ham.expectation(psi)
+    tol_g = 1e-9 if dtype == "complex128" else 1e-4
+    n_all = len(ham.shard(0, 1).shard_terms(dtype))
+    for k in (2, 3, 64):
+        shards = [ham.shard(r, k) for r in range(k)]
+        es, gs, ex = 0.0, np.zeros(a.n_params), 0.0
+        empty = 0
+        for sh in shards:
+            e, g, ws = q2.vqe_energy_grad(ans, sh, theta, dtype=dtype, want_grad=True, workspace=ws)
+            e0, _, ws = q2.vqe_energy_grad(ans, sh, theta, dtype=dtype, want_grad=False, workspace=ws)
+            ee, nrm = sh.expectation(psi)
+            assert abs(e - e0) < TOL_E[dtype] and abs(nrm - 1) < 1e-5
+            if len(sh.shard_terms(dtype)) == 0:
+                empty += 1
+                assert e == 0.0 and e0 == 0.0 and ee == 0.0 and not np.any(g)
+            es, gs, ex = es + e, gs + g, ex + ee
+        assert abs(es - e_all) < TOL_E[dtype] and abs(es - e_ref) < TOL_E[dtype]
+        assert abs(ex - e_psi) < TOL_E[dtype]
+        assert np.max(np.abs(gs - g_all)) < tol_g and np.max(np.abs(gs - g_ref)) < tol_g
+        if k == 64:
+            assert empty > 0 and n_all == w.ham.n_terms
