@@ -92,6 +92,22 @@ q2_status q2_debug_wait_probe(unsigned polls, void *stream);
  */
 q2_status q2_debug_fp64_rate(double *flops_per_s, void *stream);
 
+/*
+ * Tests only: enable (default) or disable the fast path of the rotation sweep
+ * for passes made of canonical 4-dimensional register blocks, so that both the
+ * fast path and the general block path can be checked against the oracle.
+ * Affects calls made afterwards, on every thread.
+ */
+q2_status q2_debug_sweep_fast_path(int enable);
+
+/*
+ * Tests only: enable (default) or disable the lean path of the expectation
+ * (complex64 passes of REAL and DIAG groups in blocks of at most 3 dimensions),
+ * so that both it and the general path can be checked against the oracle.
+ * Affects calls made afterwards, on every thread.
+ */
+q2_status q2_debug_expect_fast_path(int enable);
+
 #ifdef __cplusplus
 }
 #endif

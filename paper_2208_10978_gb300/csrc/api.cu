@@ -63,6 +63,8 @@ q2_status cuda_fail(cudaError_t e, const char *where) {
   } while (0)
 
 int g_tile[2] = {12, 11};       // tile qubits per dtype
+bool g_canon4_enabled = true;   // canonical 4-dimensional sweep blocks take the fast path
+bool g_lean_expect_enabled = true;   // REAL/DIAG expectation passes take the lean path
 const int g_chunk[2] = {4, 3};  // minimum contiguous low qubits per dtype (128-byte chunks)
 std::mutex g_cfg_mu;
 
@@ -192,7 +194,7 @@ q2_status plan_ham_locked(q2_ham *h, q2_dtype d) {
   if (h->planned[d]) return Q2_OK;
   try {
     h->plan[d] = build_ham_plan(h->n, (int64_t)h->c.size(), h->x.data(), h->z.data(), h->c.data(),
-                                ham_tile_bits(d), g_chunk[d]);
+                                ham_tile_bits(d), g_chunk[d], d == Q2_C64 ? LUT_STAGE_HAM_C64 : LUT_STAGE);
     restrict_to_shard(h->plan[d], h->shard, h->n_shards);
   } catch (const std::exception &e) {
     return fail(Q2_ERR_INVALID, std::string("Hamiltonian schedule: ") + e.what());
@@ -214,6 +216,10 @@ q2_status ham_tables(const q2_ham *hc, q2_dtype d, const HamPlan **plan, const D
     const HamPlan &p = h->plan[d];
     const size_t gb = sizeof(GroupDesc) * std::max<size_t>(1, p.groups.size());
     std::vector<unsigned char> lb = lut_bytes(p.lut2, d);
+    if (d == Q2_C64 && !p.lut2.empty()) {   // (R, R) for REAL and DIAG groups: the lean path reads both halves
+      const std::vector<float> f = p.lut_f32();
+      std::memcpy(lb.data(), f.data(), sizeof(float) * f.size());
+    }
     const size_t bb = sizeof(BlockDesc) * std::max<size_t>(1, p.blocks.size());
     Q2_CUDA(cudaMalloc(&t.groups, gb), "cudaMalloc(groups)");
     if (cudaMalloc(&t.lut, std::max<size_t>(16, lb.size())) != cudaSuccess ||
@@ -295,8 +301,10 @@ q2_status ansatz_tables(const q2_ansatz *ac, q2_dtype d, const RotPlan **plan, c
 template <typename R>
 cudaError_t run_sweep(R *psi, int n, const RotPlan &p, const GroupDesc *dgroups, const BlockDesc *dblocks,
                       const void *dlut, unsigned *fault, cudaStream_t st) {
-  for (const PassDesc &pd : p.passes) {
-    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dblocks, dlut, fault, st);
+  for (size_t i = 0; i < p.passes.size(); ++i) {
+    const PassDesc &pd = p.passes[i];
+    const bool c4 = i < p.pass_canon4.size() && p.pass_canon4[i] && g_canon4_enabled;
+    cudaError_t e = launch_sweep<R>(psi, n, pd, dgroups, dblocks, dlut, fault, c4, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -313,8 +321,9 @@ cudaError_t run_expect(const R *psi, int n, const HamPlan &h, const DevTables &t
     return e;
   }
   for (size_t i = 0; i < h.passes.size(); ++i) {
+    const bool lean = g_lean_expect_enabled && i < h.pass_lean.size() && h.pass_lean[i];
     cudaError_t e =
-        launch_expect<R>(psi, n, h.passes[i], t.groups, t.blocks, t.lut, partial, grid, i == 0, fault, st);
+        launch_expect<R>(psi, n, h.passes[i], t.groups, t.blocks, t.lut, partial, grid, i == 0, fault, lean, st);
     if (e != cudaSuccess) return e;
   }
   return launch_reduce_pairs(partial, grid, out2, st);
@@ -1181,6 +1190,16 @@ q2_status q2_debug_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uin
 
 int q2_debug_threads_per_cta(void) { return NT; }
 
+q2_status q2_debug_sweep_fast_path(int enable) {
+  g_canon4_enabled = enable != 0;
+  return Q2_OK;
+}
+
+q2_status q2_debug_expect_fast_path(int enable) {
+  g_lean_expect_enabled = enable != 0;
+  return Q2_OK;
+}
+
 q2_status q2_debug_enable_timing(int enable) {
   g_timing.enabled = enable != 0;
   g_timing.valid = false;
@@ -1247,6 +1266,8 @@ q2_status ham_host_plan(const q2_ham *hc, q2_dtype d, const HamPlan **plan, int 
 }
 
 int ham_qubits(const q2_ham *h) { return h->n; }
+
+bool lean_expect_enabled() { return g_lean_expect_enabled; }
 
 q2_status set_error(q2_status s, const char *msg) { return fail(s, msg); }
 

@@ -574,6 +574,158 @@ __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, co
   }
 }
 
+// ------------------------------------------------------------------ canonical 4-dimensional sweep blocks
+//
+// Fast path for passes whose register blocks are all canonical and 4-dimensional
+// with exactly four groups (group k pairs combos c and c | 1 << k and is REAL):
+// the shape of every block of a UCCSD double-excitation sweep.  Everything in a
+// group's addressing that does not depend on the tile is computed once per CTA
+// and pass:
+//   thr[g][tid]  code of the thread's coset base, blane[lane] ^ bwarp[warp];
+//   C4Group[g]   byte offset of the group's LUT in shared memory and its four
+//                pair generators (bccode[1 << i] << 4, one per block dimension);
+//   btab[b][tid] byte offset of the thread's coset base in the tile.
+// Per tile and group only the tile code is added.  Amplitudes are kept as packed
+// 64-bit (re, im) registers for the f32x2 instructions, and the combos of a coset
+// and the LUT entries of a group are walked in Gray-code order, one XOR per step.
+
+constexpr int C4_MAX_GROUPS = 16;   // groups of a pass on this path (4 blocks)
+
+struct alignas(16) C4Group {
+  uint32_t lutoff;   // byte offset of the group's LUT from the start of shared memory
+  uint32_t g01;      // pair generators of block dimensions 0 and 1 (u16 each, already << 4)
+  uint32_t g23;      // ... of dimensions 2 and 3
+  uint32_t pad;
+};
+
+__host__ __device__ inline size_t c4_extra_bytes(int ng, int nb) {
+  return align16((size_t)ng * NT) + sizeof(C4Group) * (size_t)ng + align16(sizeof(uint16_t) * NT * (size_t)nb);
+}
+
+__device__ __forceinline__ uint32_t c4_gen(const C4Group &g, int i) {
+  return i == 0 ? (g.g01 & 0xffffu) : i == 1 ? (g.g01 >> 16) : i == 2 ? (g.g23 & 0xffffu) : (g.g23 >> 16);
+}
+
+// Rotation [[c, -s], [s, c]] of a packed complex pair with C = (c, c), S = (s, s).
+__device__ __forceinline__ void rot_real_packed(unsigned long long &a, unsigned long long &b, unsigned long long C,
+                                                unsigned long long S) {
+  const unsigned long long na = f2_sub(f2_mul(C, a), f2_mul(S, b));
+  const unsigned long long nb = f2_fma(S, a, f2_mul(C, b));
+  a = na;
+  b = nb;
+}
+
+// Index of the lowest set bit of v (1 <= v < 16), usable in device constant expressions.
+__host__ __device__ constexpr int ctz_c(int v) { return (v & 1) ? 0 : (v & 2) ? 1 : (v & 4) ? 2 : 3; }
+// Gray code: step t visits t ^ (t >> 1); the bit flipped after step t is ctz(t + 1).
+__host__ __device__ constexpr int gray_flip3(int t) { return ctz_c(t + 1); }
+__host__ __device__ constexpr int gray3(int t) { return t ^ (t >> 1); }
+__host__ __device__ constexpr int gray_flip4(int t) { return ctz_c(t + 1); }
+__host__ __device__ constexpr int gray4(int t) { return t ^ (t >> 1); }
+
+// Combo c of group K's pair p (p = 0..7): the three bits other than K carry p.
+template <int K> __host__ __device__ constexpr int c4_combo(int p) {
+  return K == 0 ? (p << 1) : K == 1 ? ((p & 1) | ((p & 6) << 1)) : K == 2 ? ((p & 3) | ((p & 4) << 1)) : p;
+}
+// Block dimension of the i-th bit of a pair index of group K.
+template <int K> __host__ __device__ constexpr int c4_dim(int i) { return i < K ? i : i + 1; }
+
+// Group K of a canonical block on one coset held in v[16].
+template <int K>
+__device__ __forceinline__ void c4_group(unsigned long long (&v)[16], const unsigned char *base, uint32_t A,
+                                         const C4Group &cg) {
+  const uint32_t G0 = c4_gen(cg, c4_dim<K>(0)), G1 = c4_gen(cg, c4_dim<K>(1)), G2 = c4_gen(cg, c4_dim<K>(2));
+  uint32_t addr = A;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    constexpr int dummy = 0;
+    (void)dummy;
+    const int p = gray3(t);
+    const int c = c4_combo<K>(p);
+    const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(base + addr);
+    rot_real_packed(v[c], v[c | (1 << K)], e.x, e.y);
+    if (t < 7) {
+      const int f = gray_flip3(t);
+      addr ^= f == 0 ? G0 : f == 1 ? G1 : G2;
+    }
+  }
+}
+
+// One canonical 4-dimensional block: J cosets per thread (16 amplitudes each).
+template <int J>
+__device__ __forceinline__ void sweep_block_c4(float2 *tile, const BlockDesc &B, int b, const Stage<float, float4> &s,
+                                               const unsigned char *thr, const C4Group *cgs, const uint16_t *btab) {
+  const uint32_t tid = threadIdx.x;
+  unsigned char *tb = reinterpret_cast<unsigned char *>(tile);
+  const uint32_t W0 = (uint32_t)B.comb[1] << 3, W1 = (uint32_t)B.comb[2] << 3, W2 = (uint32_t)B.comb[4] << 3,
+                 W3 = (uint32_t)B.comb[8] << 3;
+  const int gb = B.g_begin;
+  const uint32_t bt = btab[b * NT + tid];
+#pragma unroll 1
+  for (int j = 0; j < J; ++j) {
+    unsigned long long v[16];
+    uint32_t o = (bt ^ B.uj[j]) << 3;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      v[gray4(t)] = *reinterpret_cast<const unsigned long long *>(tb + o);
+      if (t < 15) {
+        const int f = gray_flip4(t);
+        o ^= f == 0 ? W0 : f == 1 ? W1 : f == 2 ? W2 : W3;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int g = gb + k;
+      const GroupDesc &gd = s.gs[g];
+      const uint32_t cb = s.tcode[g] ^ thr[g * NT + tid] ^ gd.bjcode[j];
+      const C4Group cg = cgs[g];
+      const uint32_t A = cg.lutoff | (cb << 4);
+      if (k == 0) c4_group<0>(v, s.base, A, cg);
+      else if (k == 1) c4_group<1>(v, s.base, A, cg);
+      else if (k == 2) c4_group<2>(v, s.base, A, cg);
+      else c4_group<3>(v, s.base, A, cg);
+    }
+    // o is now the address of combo gray4(15) = 8; walk back in the same order to store
+#pragma unroll
+    for (int t = 15; t >= 0; --t) {
+      *reinterpret_cast<unsigned long long *>(tb + o) = v[gray4(t)];
+      if (t > 0) {
+        const int f = gray_flip4(t - 1);
+        o ^= f == 0 ? W0 : f == 1 ? W1 : f == 2 ? W2 : W3;
+      }
+    }
+  }
+}
+
+// Per-CTA tables of the canonical path (after stage_pass; the caller syncs).
+__device__ __forceinline__ void stage_c4(const Stage<float, float4> &s, const PassDesc &pd, unsigned char *extra,
+                                         unsigned char **thr, C4Group **cgs, uint16_t **btab) {
+  const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
+  unsigned char *t = extra;
+  C4Group *c = reinterpret_cast<C4Group *>(t + align16((size_t)ng * NT));
+  uint16_t *bt = reinterpret_cast<uint16_t *>(c + ng);
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int g = 0; g < ng; ++g) t[g * NT + tid] = s.gs[g].blane[lane] ^ s.gs[g].bwarp[warp];
+  if ((int)tid < ng) {
+    const GroupDesc &d = s.gs[tid];
+    C4Group r;
+    r.lutoff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + d.lut) - s.base);
+    r.g01 = ((uint32_t)d.bccode[1] << 4) | ((uint32_t)d.bccode[2] << 20);
+    r.g23 = ((uint32_t)d.bccode[4] << 4) | ((uint32_t)d.bccode[8] << 20);
+    r.pad = 0;
+    c[tid] = r;
+  }
+  for (int b = 0; b < nb; ++b) {
+    uint32_t v = tid;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v = insert_zero(v, s.bs[b].piv[i]);
+    bt[b * NT + tid] = (uint16_t)v;
+  }
+  *thr = t;
+  *cgs = c;
+  *btab = bt;
+}
+
 // ------------------------------------------------------------------ rotation sweep
 
 template <typename R, bool STREAM, int TT, bool GUARD>
@@ -631,6 +783,53 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
     }
     bulk_wait_all();
   }
+}
+
+// The same pass loop on the canonical 4-dimensional fast path (complex64, 12- and
+// 13-qubit tiles), as a kernel of its own so that its registers are allocated
+// for this path alone.
+template <bool STREAM, int TT>
+__global__ void __launch_bounds__(NT, 4)
+    k_sweep_c4(float *psi, int n, PassDesc pd, const GroupDesc *groups, const BlockDesc *blocks, const float2 *lut,
+               unsigned *fault) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
+  const SmemLayout L = smem_layout(sizeof(float2), pd, 1, c4_extra_bytes(ng, nb), sizeof(float4),
+                                   sizeof(float4) << R_MAX_ROT);
+  const Stage<float, float4> st = stage_pass<float, float4>(smem, pd, L, groups, blocks, lut);
+  float2 *tile = reinterpret_cast<float2 *>(smem + L.tiles);
+  __syncthreads();
+  unsigned char *thr;
+  C4Group *cgs;
+  uint16_t *btab;
+  stage_c4(st, pd, smem + L.extra, &thr, &cgs, &btab);
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (n - pd.T);
+  uint32_t parity = 0;
+  TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
+    const uint64_t base = tw.base;
+    bulk_load_tile(psi, base, st, tile, &bar);
+    tile_codes(st, ng, t);
+    const bool ok = mbar_wait(&bar, parity, fault);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
+      break;
+    }
+    for (int b = 0; b < nb; ++b) {
+      sweep_block_c4<BlockShape<TT, 4>::J>(tile, st.bs[b], b, st, thr, cgs, btab);
+      __syncthreads();
+    }
+    fence_proxy_async();
+    __syncthreads();
+    bulk_store_tile(psi, base, st, tile);
+    bulk_wait_read();
+    __syncthreads();
+  }
+  bulk_wait_all();
 }
 
 // ------------------------------------------------------------------ reductions
@@ -860,6 +1059,205 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *
       acc_n.add(s);
     }
     for (int b = 0; b < nb; ++b) expect_block_any<R, TT, GUARD>(tile, st.bs[b], st, acc_e);
+    __syncthreads();
+  }
+  const double e = block_sum(acc_e.value(), red);
+  const double nn = block_sum(acc_n.value(), red);
+  if (threadIdx.x == 0) {
+    if (first_pass) {
+      partial[2 * blockIdx.x] = e;
+      partial[2 * blockIdx.x + 1] = nn;
+    } else {
+      partial[2 * blockIdx.x] += e;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ expectation, lean path
+//
+// Passes whose groups are all REAL (real pair coefficients) or DIAG, in register
+// blocks of at most 3 dimensions, on 12- or 13-qubit tiles (complex64): each
+// thread holds all of its cosets of a block (2^TT / NT amplitudes, packed 64-bit
+// (re, im) registers) and walks every group of the block once.  The staged LUT
+// holds (R, R) for these groups, so one f32x2 multiply and one f32x2 fused
+// multiply-add give a pair's R (x_i x_j, y_i y_j); each group's sum enters the
+// compensated accumulator once.  Per group and pass the LUT byte offset and
+// the pair generators (bccode[1 << i] << 3) are staged once per CTA; the
+// combos of a coset and a group's LUT entries are walked in Gray-code order.
+
+struct alignas(16) EGroup {
+  uint32_t lutoff;   // byte offset of the group's LUT from the start of shared memory
+  uint32_t g01;      // pair generators of block dimensions 0 and 1 (u16 each, already << 3)
+  uint32_t g2;       // ... of dimension 2
+  uint32_t kind_a;   // kind | (a << 8)
+};
+
+__host__ __device__ inline size_t efast_extra_bytes(int ng) {
+  return sizeof(double) * (NT / 32) + sizeof(EGroup) * (size_t)ng;
+}
+
+__device__ __forceinline__ uint32_t egen(const EGroup &g, int i) {
+  return i == 0 ? (g.g01 & 0xffffu) : i == 1 ? (g.g01 >> 16) : g.g2;
+}
+
+__host__ __device__ constexpr int free_bit(int hb, int i) { return i < hb ? i : i + 1; }
+__host__ __device__ constexpr int deposit_free(int hb, int p) { return (p & ((1 << hb) - 1)) | ((p >> hb) << (hb + 1)); }
+__host__ __device__ constexpr int hbit(int x) { return x >= 4 ? 2 : x >= 2 ? 1 : 0; }
+
+__device__ __forceinline__ float f2_lo_plus_hi(unsigned long long v) {
+  const float2 f = f2_unpack(v);
+  return f.x + f.y;
+}
+
+// Pairs (c, c ^ X) of one REAL group over the thread's J cosets: sum of R (x_c x_p + y_c y_p).
+template <int D, int J, int X>
+__device__ __forceinline__ float efast_pairs(const unsigned long long (&v)[J][1 << D], const unsigned char *base,
+                                             uint32_t A, const uint8_t *bj, const EGroup &e) {
+  constexpr int HB = hbit(X);
+  constexpr int P = 1 << (D - 1);
+  uint32_t G[D > 1 ? D - 1 : 1];
+#pragma unroll
+  for (int i = 0; i < D - 1; ++i) G[i] = egen(e, free_bit(HB, i));
+  unsigned long long acc = 0ull;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    uint32_t a = A ^ ((uint32_t)bj[j] << 3);
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+      const int p = t ^ (t >> 1);
+      const int c = deposit_free(HB, p);
+      const unsigned long long rr = *reinterpret_cast<const unsigned long long *>(base + a);
+      acc = f2_fma(rr, f2_mul(v[j][c], v[j][c ^ X]), acc);
+      if (t + 1 < P) a ^= G[ctz_c(t + 1)];
+    }
+  }
+  return f2_lo_plus_hi(acc);
+}
+
+template <int D, int J>
+__device__ __forceinline__ float efast_switch(int x, const unsigned long long (&v)[J][1 << D], const unsigned char *base,
+                                              uint32_t A, const uint8_t *bj, const EGroup &e) {
+  switch (x) {
+#define Q2_FC(X) \
+  case X:        \
+    if constexpr (X < (1 << D)) return efast_pairs<D, J, X>(v, base, A, bj, e); \
+    break;
+    Q2_FC(1) Q2_FC(2) Q2_FC(3) Q2_FC(4) Q2_FC(5) Q2_FC(6) Q2_FC(7)
+#undef Q2_FC
+    default: break;
+  }
+  return 0.f;
+}
+
+template <int D, int J>
+__device__ __forceinline__ void expect_block_fast(const float2 *tile, const BlockDesc &B, const Stage<float> &s,
+                                                  const EGroup *egs, Kahan<float> &acc, bool norm, Kahan<float> &acc_n) {
+  constexpr int N = 1 << D;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t bt = tid;
+#pragma unroll
+  for (int i = 0; i < D; ++i) bt = insert_zero(bt, B.piv[i]);
+  uint32_t W[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) W[i] = (uint32_t)B.comb[1 << i] << 3;
+  const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile);
+  unsigned long long v[J][N];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    uint32_t o = (bt ^ B.uj[j]) << 3;
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+      v[j][t ^ (t >> 1)] = *reinterpret_cast<const unsigned long long *>(tb + o);
+      if (t + 1 < N) o ^= W[ctz_c(t + 1)];
+    }
+  }
+  if (norm) {   // every amplitude of the tile is in exactly one coset of this block
+    unsigned long long n2 = 0ull;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int c = 0; c < N; ++c) n2 = f2_fma(v[j][c], v[j][c], n2);
+    acc_n.add(f2_lo_plus_hi(n2));
+  }
+#pragma unroll 1
+  for (int gi = B.g_begin; gi < B.g_end; ++gi) {
+    const GroupDesc &g = s.gs[gi];
+    const EGroup e = egs[gi];
+    const uint32_t cb = s.tcode[gi] ^ g.blane[lane] ^ g.bwarp[warp];
+    const uint32_t A = e.lutoff | (cb << 3);
+    const int kind = (int)(e.kind_a & 0xffu);
+    float sum;
+    if (kind == KIND_DIAG) {
+      unsigned long long a2 = 0ull;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        uint32_t a = A ^ ((uint32_t)g.bjcode[j] << 3);
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+          const int c = t ^ (t >> 1);
+          const unsigned long long rr = *reinterpret_cast<const unsigned long long *>(s.base + a);
+          a2 = f2_fma(rr, f2_mul(v[j][c], v[j][c]), a2);
+          if (t + 1 < N) a ^= egen(e, ctz_c(t + 1));
+        }
+      }
+      sum = f2_lo_plus_hi(a2);
+    } else {
+      sum = 2.f * efast_switch<D, J>((int)(e.kind_a >> 8), v, s.base, A, g.bjcode, e);
+    }
+    acc.add(sum);
+  }
+}
+
+template <int TT>
+__device__ __forceinline__ void expect_block_fast_any(const float2 *tile, const BlockDesc &B, const Stage<float> &s,
+                                                      const EGroup *egs, Kahan<float> &acc, bool norm,
+                                                      Kahan<float> &acc_n) {
+  switch (B.d) {
+    case 1: expect_block_fast<1, BlockShape<TT, 1>::J>(tile, B, s, egs, acc, norm, acc_n); break;
+    case 2: expect_block_fast<2, BlockShape<TT, 2>::J>(tile, B, s, egs, acc, norm, acc_n); break;
+    default: expect_block_fast<3, BlockShape<TT, 3>::J>(tile, B, s, egs, acc, norm, acc_n); break;
+  }
+}
+
+template <bool STREAM, int TT>
+__global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, PassDesc pd, const GroupDesc *groups,
+                                                       const BlockDesc *blocks, const float2 *lut, double *partial,
+                                                       int first_pass, unsigned *fault) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
+  const SmemLayout L = smem_layout(sizeof(float2), pd, 1, efast_extra_bytes(ng), sizeof(float2),
+                                   sizeof(float2) << R_MAX);
+  const Stage<float> st = stage_pass<float>(smem, pd, L, groups, blocks, lut);
+  float2 *tile = reinterpret_cast<float2 *>(smem + L.tiles);
+  double *red = reinterpret_cast<double *>(smem + L.extra);
+  EGroup *egs = reinterpret_cast<EGroup *>(red + NT / 32);
+  __syncthreads();
+  if ((int)threadIdx.x < ng) {
+    const GroupDesc &d = st.gs[threadIdx.x];
+    EGroup r;
+    r.lutoff = (uint32_t)(reinterpret_cast<const unsigned char *>(st.lut + d.lut) - st.base);
+    r.g01 = ((uint32_t)d.bccode[1] << 3) | ((uint32_t)d.bccode[2] << 19);
+    r.g2 = (uint32_t)d.bccode[4] << 3;
+    r.kind_a = (uint32_t)d.kind | ((uint32_t)d.a << 8);
+    egs[threadIdx.x] = r;
+  }
+  const uint64_t ntiles = 1ull << (n - pd.T);
+  Kahan<float> acc_e, acc_n;
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t parity = 0;
+  TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
+    bulk_load_tile(psi, tw.base, st, tile, &bar);
+    tile_codes(st, ng, t);
+    const bool ok = mbar_wait(&bar, parity, fault);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
+      break;
+    }
+    for (int b = 0; b < nb; ++b) expect_block_fast_any<TT>(tile, st.bs[b], st, egs, acc_e, first_pass && b == 0, acc_n);
     __syncthreads();
   }
   const double e = block_sum(acc_e.value(), red);
@@ -1670,7 +2068,7 @@ int blocks_per_sm(K kernel, size_t smem) {
 // per-function state shared by every host thread, so it is always set to this
 // fixed value, never to one launch's size.
 size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry_bytes = 0,
-                  size_t lut_align = 16) {
+                  size_t lut_align = 16, int lut_max = LUT_STAGE) {
   if (lut_entry_bytes == 0) lut_entry_bytes = amp_bytes;
   PassDesc pd{};
   pd.T = T <= 8 ? 8 : T;
@@ -1679,7 +2077,7 @@ size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry
   pd.g_end = G_STAGE;
   pd.b_begin = 0;
   pd.b_end = G_STAGE;
-  pd.lut_count = LUT_STAGE;
+  pd.lut_count = lut_max;
   SmemLayout L;
   size_t o = 0;
   o = align16(o + (size_t)amp_bytes * ((size_t)1 << pd.T) * vectors);
@@ -1687,7 +2085,7 @@ size_t worst_smem(int amp_bytes, int T, int vectors, size_t extra, int lut_entry
   o = align16(o + sizeof(GroupDesc) * G_STAGE);
   o = align16(o + sizeof(BlockDesc) * G_STAGE);
   o = align_to(o, lut_align);
-  o = align16(o + (size_t)lut_entry_bytes * LUT_STAGE);
+  o = align16(o + (size_t)lut_entry_bytes * lut_max);
   o = align16(o + sizeof(uint32_t) * G_STAGE);
   o = align16(o + extra);
   (void)L;
@@ -1733,6 +2131,9 @@ bool streaming(int n, int bytes) { return ((uint64_t)bytes << n) > (64ull << 20)
       default: return st_ ? &KERNEL<R, true, 9, true> : &KERNEL<R, false, 9, true>;      \
     }                                                                                     \
   }()
+
+// Largest LUT of a Hamiltonian pass for a dtype (entries staged in shared memory).
+template <typename R> constexpr int ham_lut_max() { return sizeof(R) == 4 ? LUT_STAGE_HAM_C64 : LUT_STAGE; }
 
 PassDesc worst_pass(int T, int C) {
   PassDesc pd{};
@@ -1814,9 +2215,9 @@ cudaError_t measure_fp64_rate(double *flops_per_s, cudaStream_t st) {
 }
 
 size_t tile_smem_bytes(int amp_bytes, int T, int C, int vectors) {
-  return smem_layout(amp_bytes, worst_pass(T, C), vectors, sizeof(double) * (NT / 32), amp_bytes,
-                     (size_t)amp_bytes << R_MAX)
-      .total;
+  PassDesc wp = worst_pass(T, C);
+  wp.lut_count = amp_bytes == 8 ? LUT_STAGE_HAM_C64 : LUT_STAGE;
+  return smem_layout(amp_bytes, wp, vectors, sizeof(double) * (NT / 32), amp_bytes, (size_t)amp_bytes << R_MAX).total;
 }
 
 size_t reverse_smem_bytes(int amp_bytes, int T, int C) {
@@ -1845,10 +2246,30 @@ cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st) {
 
 template <typename R>
 cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                         const BlockDesc *blocks, const void *lut, unsigned *fault, cudaStream_t st) {
+                         const BlockDesc *blocks, const void *lut, unsigned *fault, bool c4, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const int nvec = 1;
   const int eb = (int)sizeof(typename SweepLut<R>::E);
+  if constexpr (sizeof(R) == 4 && Q2_F32X2) {
+    if (c4 && (pd.T == 12 || pd.T == 13) && pd.g_end - pd.g_begin <= C4_MAX_GROUPS) {
+      const size_t smem =
+          smem_layout(sizeof(C2), pd, nvec, c4_extra_bytes(pd.g_end - pd.g_begin, pd.b_end - pd.b_begin), eb,
+                      (size_t)eb << R_MAX_ROT).total;
+      const bool st_ = streaming(n, 2 * (int)sizeof(R));
+      auto k = pd.T == 12 ? (st_ ? &k_sweep_c4<true, 12> : &k_sweep_c4<false, 12>)
+                          : (st_ ? &k_sweep_c4<true, 13> : &k_sweep_c4<false, 13>);
+      PassDesc wp = worst_pass(pd.T, pd.C);
+      wp.g_end = C4_MAX_GROUPS;
+      wp.b_end = C4_MAX_GROUPS / 4;
+      cudaError_t e = prepare(k, smem_layout(sizeof(C2), wp, nvec, c4_extra_bytes(C4_MAX_GROUPS, C4_MAX_GROUPS / 4), eb,
+                                             (size_t)eb << R_MAX_ROT).total);
+      if (e != cudaSuccess) return e;
+      const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
+      k<<<grid, NT, smem, st>>>(reinterpret_cast<float *>(psi), n, pd, groups, blocks,
+                                reinterpret_cast<const float2 *>(lut), fault);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = smem_layout(sizeof(C2), pd, nvec, 0, eb, (size_t)eb << R_MAX_ROT).total;
   auto k = Q2_DISPATCH(k_sweep, R, n, pd.T);
   cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, 0, eb, (size_t)eb << R_MAX_ROT));
@@ -1864,21 +2285,38 @@ int expect_grid(int n, int T, int C) {
   const int nvec = 1;
   const size_t smem = tile_smem_bytes(sizeof(C2), T, C, nvec);
   auto k = Q2_DISPATCH(k_expect, R, n, T);
-  prepare(k, worst_smem(sizeof(C2), T, nvec, sizeof(double) * (NT / 32), sizeof(C2), sizeof(C2) << R_MAX));
+  prepare(k, worst_smem(sizeof(C2), T, nvec, sizeof(double) * (NT / 32), sizeof(C2), sizeof(C2) << R_MAX,
+                        ham_lut_max<R>()));
   return (int)grid_for(1ull << (n - T), blocks_per_sm(k, smem));
 }
 
 template <typename R>
 cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
                           const BlockDesc *blocks, const void *lut, double *partial, int grid, bool first,
-                          unsigned *fault, cudaStream_t st) {
+                          unsigned *fault, bool lean, cudaStream_t st) {
   using C2 = typename Vec2<R>::type;
   const int nvec = 1;
+  if constexpr (sizeof(R) == 4) {
+    if (lean && (pd.T == 12 || pd.T == 13)) {
+      const int ng = pd.g_end - pd.g_begin;
+      const size_t smem =
+          smem_layout(sizeof(C2), pd, nvec, efast_extra_bytes(ng), sizeof(C2), sizeof(C2) << R_MAX).total;
+      const bool st_ = streaming(n, 2 * (int)sizeof(R));
+      auto k = pd.T == 12 ? (st_ ? &k_expect_fast<true, 12> : &k_expect_fast<false, 12>)
+                          : (st_ ? &k_expect_fast<true, 13> : &k_expect_fast<false, 13>);
+      cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, efast_extra_bytes(G_STAGE), sizeof(C2),
+                                            sizeof(C2) << R_MAX, ham_lut_max<R>()));
+      if (e != cudaSuccess) return e;
+      k<<<grid, NT, smem, st>>>(reinterpret_cast<const float *>(psi), n, pd, groups, blocks,
+                                reinterpret_cast<const float2 *>(lut), partial, first ? 1 : 0, fault);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem =
       smem_layout(sizeof(C2), pd, nvec, sizeof(double) * (NT / 32), sizeof(C2), sizeof(C2) << R_MAX).total;
   auto k = Q2_DISPATCH(k_expect, R, n, pd.T);
   cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, sizeof(double) * (NT / 32), sizeof(C2),
-                                        sizeof(C2) << R_MAX));
+                                        sizeof(C2) << R_MAX, ham_lut_max<R>()));
   if (e != cudaSuccess) return e;
   k<<<grid, NT, smem, st>>>(psi, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), partial,
                             first ? 1 : 0, fault);
@@ -1906,7 +2344,7 @@ cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const
       case 12: k = &k_happly_blk<R, 12>; break;
       default: k = &k_happly_blk<R, 13>; break;
     }
-    cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0, sizeof(C2), al));
+    cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0, sizeof(C2), al, ham_lut_max<R>()));
     if (e != cudaSuccess) return e;
     const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
     k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), first ? 1 : 0,
@@ -1917,7 +2355,7 @@ cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const
   pq.b_begin = pq.b_end = 0;
   const size_t smem = smem_layout(sizeof(C2), pq, 2, 0).total;
   auto k = Q2_DISPATCH(k_happly, R, n, pd.T);
-  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0));
+  cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0, 0, 16, ham_lut_max<R>()));
   if (e != cudaSuccess) return e;
   const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
   k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, reinterpret_cast<const C2 *>(lut), first ? 1 : 0);
@@ -1984,11 +2422,12 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
 #define Q2_INST(R)                                                                                  \
   template cudaError_t launch_init_hf<R>(R *, int, int, cudaStream_t);                             \
   template cudaError_t launch_sweep<R>(R *, int, const PassDesc &, const GroupDesc *,              \
-                                       const BlockDesc *, const void *, unsigned *, cudaStream_t);  \
+                                       const BlockDesc *, const void *, unsigned *, bool,           \
+                                       cudaStream_t);                                               \
   template int expect_grid<R>(int, int, int);                                                       \
   template cudaError_t launch_expect<R>(const R *, int, const PassDesc &, const GroupDesc *,        \
                                         const BlockDesc *, const void *, double *, int, bool,       \
-                                        unsigned *, cudaStream_t);                                  \
+                                        unsigned *, bool, cudaStream_t);                            \
   template cudaError_t launch_happly<R>(const R *, R *, int, const PassDesc &, const GroupDesc *,   \
                                         const BlockDesc *, const void *, bool, unsigned *,          \
                                         cudaStream_t);                                              \

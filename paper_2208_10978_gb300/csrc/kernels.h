@@ -24,12 +24,12 @@ cudaError_t measure_fp64_rate(double *flops_per_s, cudaStream_t st);
 template <typename R> cudaError_t launch_init_hf(R *psi, int n, int n_elec, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
-                         const BlockDesc *blocks, const void *lut, unsigned *fault, cudaStream_t st);
+                         const BlockDesc *blocks, const void *lut, unsigned *fault, bool canon4, cudaStream_t st);
 template <typename R> int expect_grid(int n, int T, int C);
 template <typename R>
 cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDesc *groups,
                           const BlockDesc *blocks, const void *lut, double *partial, int grid, bool first,
-                          unsigned *fault, cudaStream_t st);
+                          unsigned *fault, bool lean, cudaStream_t st);
 template <typename R>
 cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const GroupDesc *groups,
                           const BlockDesc *blocks, const void *lut, bool first, unsigned *fault,

@@ -26,6 +26,7 @@ namespace q2 {
 q2_status ham_host_plan(const q2_ham *h, q2_dtype d, const HamPlan **plan, int *chunk);
 int ham_qubits(const q2_ham *h);
 q2_status set_error(q2_status s, const char *msg);
+bool lean_expect_enabled();
 }  // namespace q2
 
 using namespace q2;
@@ -101,7 +102,9 @@ cudaError_t run(const R *psi, int n, const HamPlan &h, const GroupDesc *groups, 
     return e;
   }
   for (size_t i = 0; i < h.passes.size(); ++i) {
-    cudaError_t e = launch_expect<R>(psi, n, h.passes[i], groups, blocks, lut, partial, grid, i == 0, fault, st);
+    const bool lean = lean_expect_enabled() && i < h.pass_lean.size() && h.pass_lean[i];
+    cudaError_t e =
+        launch_expect<R>(psi, n, h.passes[i], groups, blocks, lut, partial, grid, i == 0, fault, lean, st);
     if (e != cudaSuccess) return e;
   }
   return launch_reduce_pairs(partial, grid, out, st);
@@ -143,9 +146,8 @@ extern "C" q2_status q2_expectation_noalloc(const void *psi_dev, int n, q2_dtype
 
   std::vector<float> lutf;
   const void *lut_src = hp->lut2.data();
-  if (dtype == Q2_C64) {
-    lutf.resize(hp->lut2.size());
-    for (size_t i = 0; i < lutf.size(); ++i) lutf[i] = (float)hp->lut2[i];
+  if (dtype == Q2_C64) {   // (R, R) for REAL and DIAG groups, as the handle's own device LUT
+    lutf = hp->lut_f32();
     lut_src = lutf.data();
   }
   double *out = reinterpret_cast<double *>(base);

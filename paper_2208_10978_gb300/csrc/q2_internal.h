@@ -42,6 +42,7 @@ constexpr int P_MAX = 32;        // max per-thread diagonal iterations over a ti
 constexpr int RP_MAX = 512;      // max rotations in one pass (reverse-sweep partials)
 constexpr int G_STAGE = 64;      // max groups per pass (staged in shared memory)
 constexpr int LUT_STAGE = 1024;  // max LUT entries per pass (staged in shared memory)
+constexpr int LUT_STAGE_HAM_C64 = 2048;  // ... for Hamiltonian passes in complex64 (8-byte entries)
 constexpr int T_MIN = 8;
 constexpr int T_LIMIT = 13;
 
@@ -144,6 +145,9 @@ struct RotPlan {
   std::vector<double> wlut;
   std::vector<double> fold;
   std::vector<uint8_t> pass_one_param;   // every group of the pass is a one-parameter group
+  // Every block of the pass is canonical, 4-dimensional and holds exactly its four
+  // pairing groups (the sweep's fast path), and the pass has at most 16 groups.
+  std::vector<uint8_t> pass_canon4;
   // LUT of (cos b, sin b) for every group and code, b = sum_k sign_k(code) phi_k / 2.
   void build_lut(const double *phi, double *lut2) const;
 };
@@ -161,6 +165,12 @@ struct HamPlan {
   // Hamiltonian's term arrays (groups as stored, i.e. after block reordering).
   std::vector<int64_t> term_idx;
   std::vector<int64_t> term_begin;
+  // Every group of the pass is REAL or DIAG and every block has at most 3
+  // dimensions (the expectation's lean path).
+  std::vector<uint8_t> pass_lean;
+  // Device image of the LUT for the lean path in single precision: (R, R) for REAL
+  // and DIAG groups (whose Q is 0), (R, Q) otherwise.
+  std::vector<float> lut_f32() const;
 };
 
 // Keep only the passes that shard `shard` of `n_shards` evaluates: passes are
@@ -172,7 +182,7 @@ void restrict_to_shard(HamPlan &p, int shard, int n_shards);
 RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *z, int T, int C);
 void set_param_weights(RotPlan &p, const int32_t *param, const double *coef);
 HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z,
-                       const double *c, int T, int C);
+                       const double *c, int T, int C, int lut_stage = LUT_STAGE);
 int64_t count_x_groups(int64_t n_terms, const uint64_t *x);
 
 // ---- bit helpers (host and device)

@@ -401,6 +401,12 @@ RotPlan build_rot_plan(int n, int64_t n_rot, const uint64_t *x, const uint64_t *
     pd.b_end = (int)P.blocks.size();
     pd.rot_end = (int)(groups[pr.ge - 1].members.back() + 1);
     P.max_pass_rots = std::max(P.max_pass_rots, pd.rot_end - pd.rot_begin);
+    bool canon4 = pd.g_end - pd.g_begin <= 16 && pd.b_end > pd.b_begin;
+    for (int b = pd.b_begin; b < pd.b_end && canon4; ++b) {
+      const BlockDesc &bd = P.blocks[b];
+      canon4 = bd.d == 4 && bd.canon == 4 && bd.g_end - bd.g_begin == 4;
+    }
+    P.pass_canon4.push_back(canon4 ? 1 : 0);
     P.passes.push_back(pd);
   }
   P.lut_entries = lut;
@@ -455,7 +461,7 @@ void RotPlan::build_lut(const double *phi, double *lut2) const {
 // --------------------------------------------------------------- Hamiltonian
 
 HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t *z,
-                       const double *c, int Tmax, int Cmin) {
+                       const double *c, int Tmax, int Cmin, int lut_stage) {
   HamPlan H;
   H.n = n;
   const int T = std::min(Tmax, n);
@@ -508,7 +514,7 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       if (popc64(groups[g].x | lowmask) <= T) continue;
       const int nl = 1 << groups[g].basis.rank();
       if ((!W.contains(groups[g].x) && W.rank() >= T) || (int)cur.size() >= G_STAGE ||
-          align_up_int(luts, nl) + nl > LUT_STAGE) {
+          align_up_int(luts, nl) + nl > lut_stage) {
         luts = 0;
         pass_groups.push_back(cur);
         pass_gens.push_back(gens);
@@ -536,7 +542,7 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       for (size_t g = 0; g < groups.size() && !full; ++g)
         if (!done[g] && (groups[g].x & ~L) == 0) {
           const int nl = 1 << groups[g].basis.rank();
-          if ((int)chosen.size() >= G_STAGE || align_up_int(luts, nl) + nl > LUT_STAGE) {
+          if ((int)chosen.size() >= G_STAGE || align_up_int(luts, nl) + nl > lut_stage) {
             full = true;
             break;
           }
@@ -642,6 +648,11 @@ HamPlan build_ham_plan(int n, int64_t n_terms, const uint64_t *x, const uint64_t
       raw_of[g] = it->second;
     }
     pd.b_end = (int)H.blocks.size();
+    bool lean = true;
+    for (int g = pd.g_begin; g < pd.g_end; ++g)
+      lean = lean && (H.groups[g].kind == KIND_REAL || H.groups[g].kind == KIND_DIAG);
+    for (int b = pd.b_begin; b < pd.b_end; ++b) lean = lean && H.blocks[b].d <= 3;
+    H.pass_lean.push_back(lean ? 1 : 0);
     H.passes.push_back(pd);
   }
   H.lut_entries = lut;
@@ -673,9 +684,24 @@ void restrict_to_shard(HamPlan &p, int shard, int n_shards) {
     load[best] += cost[i];
   }
   std::vector<PassDesc> keep;
+  std::vector<uint8_t> keep_lean;
   for (size_t i = 0; i < np; ++i)
-    if (owner[i] == shard) keep.push_back(p.passes[i]);
+    if (owner[i] == shard) {
+      keep.push_back(p.passes[i]);
+      keep_lean.push_back(i < p.pass_lean.size() ? p.pass_lean[i] : 0);
+    }
   p.passes.swap(keep);
+  p.pass_lean.swap(keep_lean);
+}
+
+std::vector<float> HamPlan::lut_f32() const {
+  std::vector<float> f(lut2.size());
+  for (size_t i = 0; i < lut2.size(); ++i) f[i] = (float)lut2[i];
+  for (const GroupDesc &g : groups) {
+    if (g.kind != KIND_REAL && g.kind != KIND_DIAG) continue;
+    for (uint32_t c = 0; c < (1u << g.r); ++c) f[2 * (size_t)(g.lut + c) + 1] = f[2 * (size_t)(g.lut + c)];
+  }
+  return f;
 }
 
 }  // namespace q2

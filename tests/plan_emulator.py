@@ -367,3 +367,83 @@ def reverse_weighted(psi, lam, n, passes, groups, lut, signmask, wlut, NT):
         psi[idx] = tp
         lam[idx] = tl
     return psi, lam, g_out
+
+
+def _gray(t):
+    return t ^ (t >> 1)
+
+
+def _ctz(v):
+    return (v & -v).bit_length() - 1
+
+
+def pass_is_canon4(pd, blocks):
+    """The sweep fast path's condition: every block canonical, 4-dimensional, exactly 4 groups."""
+    if pd["g_end"] - pd["g_begin"] > 16 or pd["b_end"] <= pd["b_begin"]:
+        return False
+    for b in blocks[int(pd["b_begin"]):int(pd["b_end"])]:
+        if not (int(b["d"]) == 4 and int(b["canon"]) == 4 and int(b["g_end"]) - int(b["g_begin"]) == 4):
+            return False
+    return True
+
+
+def sweep_c4(psi, n, passes, groups, blocks, lut, NT, lut_base=5 * 1024):
+    """The sweep's canonical 4-dimensional fast path, with its exact address arithmetic:
+    byte offsets of amplitudes (8 bytes) walked in Gray-code order over the block's four
+    combo generators W_i = comb[1 << i] << 3 from the coset base (base(tid) ^ uj[j]) << 3;
+    per group K, the LUT byte address A = lutoff | (code << 4) with
+    code = tilecode ^ (blane[lane] ^ bwarp[warp]) ^ bjcode[j], walked in Gray-code order
+    over the three pair generators bccode[1 << i] << 4 (i != K).  lutoff is the group's
+    LUT offset (16-byte entries) from a 1 KiB-aligned staged LUT start `lut_base`.
+    Passes that do not qualify take the general walk."""
+    psi = psi.copy()
+    for pd in passes:
+        if not pass_is_canon4(pd, blocks):
+            psi = sweep(psi, n, pd[None], groups, blocks, lut, NT)
+            continue
+        T = int(pd["T"])
+        idx = tile_index(n, pd)
+        tile = psi[idx]
+        ntiles = tile.shape[0]
+        g0 = int(pd["g_begin"])
+        tid = np.arange(NT, dtype=np.int64)
+        lane, warp = tid % 32, tid // 32
+        J = (1 << (T - 4)) // NT
+        for bi in range(int(pd["b_begin"]), int(pd["b_end"])):
+            b = blocks[bi]
+            bt = tid.astype(np.uint64)
+            for i in range(4):
+                bt = _insert0(bt, int(b["piv"][i]))
+            bt = bt.astype(np.int64)
+            W = [int(b["comb"][1 << i]) << 3 for i in range(4)]
+            for j in range(J):
+                o = (bt ^ int(b["uj"][j])) << 3
+                addr = {}
+                for t in range(16):
+                    addr[_gray(t)] = o.copy()
+                    if t < 15:
+                        o = o ^ W[_ctz(t + 1)]
+                assert all(np.all(a % 8 == 0) for a in addr.values())
+                v = {c: tile[:, addr[c] >> 3] for c in range(16)}          # [t, tid]
+                for k in range(4):
+                    g = groups[g0 + int(b["g_begin"]) + k]
+                    lutoff = lut_base + (int(g["lut"]) - int(pd["lut_begin"])) * 16
+                    thr = g["blane"][lane].astype(np.int64) ^ g["bwarp"][warp].astype(np.int64)
+                    cb = _tilecode(g, T, ntiles)[:, None] ^ thr[None, :] ^ int(g["bjcode"][j])
+                    A = lutoff | (cb << 4)
+                    dims = [d for d in range(4) if d != k]
+                    G = [int(g["bccode"][1 << d]) << 4 for d in dims]
+                    a = A.copy()
+                    for t in range(8):
+                        p = _gray(t)
+                        c = sum(((p >> i) & 1) << dims[i] for i in range(3))
+                        e = (a - lut_base) // 16 + int(pd["lut_begin"])
+                        cc, ss = lut[e, 0], lut[e, 1]
+                        x, y = v[c], v[c | (1 << k)]
+                        v[c], v[c | (1 << k)] = cc * x - ss * y, ss * x + cc * y
+                        if t < 7:
+                            a = a ^ G[_ctz(t + 1)]
+                for c in range(16):
+                    tile[:, addr[c] >> 3] = v[c]
+        psi[idx] = tile
+    return psi

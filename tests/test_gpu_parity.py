@@ -371,3 +371,60 @@ def test_hamiltonian_shards_sum_to_whole(dtype):
         assert np.max(np.abs(gs - g_all)) < tol_g and np.max(np.abs(gs - g_ref)) < tol_g
         if k == 64:
             assert empty > 0 and n_all == w.ham.n_terms
+
+
+@pytest.mark.parametrize("n", [17, 20])
+def test_sweep_fast_path_and_general_path_match_oracle(n):
+    """Random-order UCCSD sweep (whole double excitations, 12-qubit tiles): nearly every pass
+    is made of canonical 4-dimensional blocks and takes the fast path (k_sweep_c4); the same
+    sweep with the fast path switched off takes the general block path.  Both match the
+    oracle per amplitude, complex64."""
+    import ctypes
+    from synth.workloads import sweep_ansatz
+    L = q2.lib()
+    L.q2_debug_sweep_fast_path.argtypes = [ctypes.c_int]
+    ans, theta = sweep_ansatz(n, n // 2, 600, n)
+    phi = ans.angles(theta)
+    rng = np.random.default_rng(n)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    ref = c_oracle.apply_rotations(psi0, n, ans.x, ans.z, phi)
+    out = {}
+    try:
+        for fast in (1, 0):
+            L.q2_debug_sweep_fast_path(fast)
+            psi = to_dev(psi0, "complex64")
+            q2.apply_pauli_rotations(psi, n, ans.x, ans.z, phi)
+            q2.async_status()
+            out[fast] = to_host(psi)
+    finally:
+        L.q2_debug_sweep_fast_path(1)
+    for fast in (1, 0):
+        assert np.max(np.abs(out[fast] - ref)) < TOL_AMP["complex64"], fast
+
+
+@pytest.mark.parametrize("n,seed", [(18, 0), (20, 1)])
+def test_expectation_fast_path_and_general_path_match_oracle(n, seed):
+    """The expectation's lean path (k_expect_fast: complex64 passes of REAL and DIAG groups in
+    blocks of at most 3 dimensions, 13-qubit tiles) and the general path give the oracle's
+    energy and norm on a random normalised state, for whole xmask groups of a UCCSD
+    Hamiltonian (every group of a real-integral Hamiltonian is REAL or DIAG)."""
+    import ctypes
+    from synth.workloads import sweep32
+    L = q2.lib()
+    L.q2_debug_expect_fast_path.argtypes = [ctypes.c_int]
+    w = sweep32(seed=seed, n=n, n_elec=n // 2, n_rot=16, min_terms=3000)
+    rng = np.random.default_rng(seed)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    num, nrm_ref = c_oracle.expectation(psi0, n, w.ham.x, w.ham.z, w.ham.c)
+    psi = to_dev(psi0, "complex64")
+    ham = q2.Hamiltonian(n, w.ham.x, w.ham.z, w.ham.c)
+    try:
+        for fast in (1, 0):
+            L.q2_debug_expect_fast_path(fast)
+            e, nrm = ham.expectation(psi)
+            assert abs(e - num / nrm_ref) < TOL_E["complex64"], fast
+            assert abs(nrm - nrm_ref) < 1e-5, fast
+    finally:
+        L.q2_debug_expect_fast_path(1)

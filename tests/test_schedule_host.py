@@ -323,3 +323,23 @@ def test_tile_walk_masked_add():
             assert base == deposit(t, m)
             base = ((base | (~m & full)) + step) & m
             t += g
+
+
+@pytest.mark.parametrize("n,T,seed", [(17, 12, 2), (17, 12, 5)])
+def test_sweep_fast_path_walk_matches_oracle(lib, n, T, seed):
+    """The canonical 4-dimensional fast path of the sweep (k_sweep_c4): its Gray-code
+    walks over amplitude byte offsets and LUT byte addresses, on the real schedule of a
+    random-order UCCSD sweep (whole double excitations, as in the 32-qubit workload),
+    reproduce the oracle's state; most passes qualify for the fast path."""
+    from synth.workloads import sweep_ansatz
+    ans, theta = sweep_ansatz(n, n // 2, 500, seed)
+    phi = ans.angles(theta)
+    passes, groups, blocks, lut, sm = emu.rot_plan(lib, n, ans.x, ans.z, phi, T, 4)
+    c4 = [emu.pass_is_canon4(pd, blocks) for pd in passes]
+    assert sum(c4) >= 0.8 * len(passes)
+    rng = np.random.default_rng(seed)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    ref = sv.apply_rotations(psi0, ans.x, ans.z, phi)
+    got = emu.sweep_c4(psi0, n, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta())
+    assert np.max(np.abs(got - ref)) < 1e-12
