@@ -80,7 +80,7 @@ __host__ __device__ inline size_t align_to(size_t v, size_t a) { return (v + a -
 
 __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc &pd, int vectors,
                                                   size_t extra_bytes, int lut_entry_bytes = 0,
-                                                  size_t lut_align = 16) {
+                                                  size_t lut_align = 16, size_t lut_slack = 0) {
   if (lut_entry_bytes == 0) lut_entry_bytes = amp_bytes;
   SmemLayout L;
   size_t o = 0;
@@ -94,7 +94,7 @@ __host__ __device__ inline SmemLayout smem_layout(int amp_bytes, const PassDesc 
   o = align16(o + sizeof(BlockDesc) * (size_t)(pd.b_end - pd.b_begin));
   o = align_to(o, lut_align);
   L.lut = o;
-  o = align16(o + (size_t)lut_entry_bytes * (size_t)pd.lut_count);
+  o = align16(o + (size_t)lut_entry_bytes * (size_t)pd.lut_count + lut_slack);
   L.tcode = o;
   o = align16(o + sizeof(uint32_t) * (size_t)(pd.g_end - pd.g_begin));
   L.extra = o;
@@ -145,7 +145,7 @@ template <typename R, typename E = typename Vec2<R>::type>
 __device__ __forceinline__ Stage<R, E> stage_pass(unsigned char *smem, const PassDesc &pd,
                                                   const SmemLayout &L, const GroupDesc *groups,
                                                   const BlockDesc *blocks,
-                                                  const typename Vec2<R>::type *lut) {
+                                                  const typename Vec2<R>::type *lut, uint32_t lut_shift = 0) {
   using C2 = typename Vec2<R>::type;
   Stage<R, E> t;
   t.T = pd.T;
@@ -161,7 +161,7 @@ __device__ __forceinline__ Stage<R, E> stage_pass(unsigned char *smem, const Pas
   }
   copy16(smem + L.groups, groups + pd.g_begin, pd.g_end - pd.g_begin);
   if (blocks) copy16(smem + L.blocks, blocks + pd.b_begin, pd.b_end - pd.b_begin);
-  E *ld = reinterpret_cast<E *>(smem + L.lut);
+  E *ld = reinterpret_cast<E *>(smem + L.lut + lut_shift);
   for (int i = threadIdx.x; i < pd.lut_count; i += NT) {
     const C2 e = __ldg(lut + pd.lut_begin + i);
     if constexpr (sizeof(E) == sizeof(C2)) ld[i] = e;
@@ -267,6 +267,26 @@ __device__ unsigned int g_async_faults;
 constexpr uint32_t WAIT_POLLS = 1u << 22;   // try_wait polls before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Bytes to add to region offset `off` of the dynamic shared memory so that the
+// region starts at a multiple of `align` (a power of two) in the shared window:
+// then a table address that is that start | (index << log2(entry)) is an
+// absolute shared address walked by XOR alone.  The layout reserves `align`
+// bytes of slack after the region.
+__device__ __forceinline__ uint32_t abs_align_shift(const unsigned char *smem, size_t off, size_t align) {
+  const uint32_t a = smem_u32(smem + off);
+  return (uint32_t)((align - (a & (align - 1))) & (align - 1));
+}
+__device__ __forceinline__ unsigned long long lds_b64(uint32_t addr) {
+  unsigned long long v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ ulonglong2 lds_b128(uint32_t addr) {
+  ulonglong2 v;
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
+  return v;
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -592,7 +612,7 @@ __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, co
 constexpr int C4_MAX_GROUPS = 16;   // groups of a pass on this path (4 blocks)
 
 struct alignas(16) C4Group {
-  uint32_t lutoff;   // byte offset of the group's LUT from the start of shared memory
+  uint32_t lutoff;   // shared-window address of the group's LUT (a multiple of its size)
   uint32_t g01;      // pair generators of block dimensions 0 and 1 (u16 each, already << 4)
   uint32_t g23;      // ... of dimensions 2 and 3
   uint32_t pad;
@@ -632,8 +652,7 @@ template <int K> __host__ __device__ constexpr int c4_dim(int i) { return i < K 
 
 // Group K of a canonical block on one coset held in v[16].
 template <int K>
-__device__ __forceinline__ void c4_group(unsigned long long (&v)[16], const unsigned char *base, uint32_t A,
-                                         const C4Group &cg) {
+__device__ __forceinline__ void c4_group(unsigned long long (&v)[16], uint32_t A, const C4Group &cg) {
   const uint32_t G0 = c4_gen(cg, c4_dim<K>(0)), G1 = c4_gen(cg, c4_dim<K>(1)), G2 = c4_gen(cg, c4_dim<K>(2));
   uint32_t addr = A;
 #pragma unroll
@@ -642,7 +661,7 @@ __device__ __forceinline__ void c4_group(unsigned long long (&v)[16], const unsi
     (void)dummy;
     const int p = gray3(t);
     const int c = c4_combo<K>(p);
-    const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(base + addr);
+    const ulonglong2 e = lds_b128(addr);
     rot_real_packed(v[c], v[c | (1 << K)], e.x, e.y);
     if (t < 7) {
       const int f = gray_flip3(t);
@@ -680,10 +699,10 @@ __device__ __forceinline__ void sweep_block_c4(float2 *tile, const BlockDesc &B,
       const uint32_t cb = s.tcode[g] ^ thr[g * NT + tid] ^ gd.bjcode[j];
       const C4Group cg = cgs[g];
       const uint32_t A = cg.lutoff | (cb << 4);
-      if (k == 0) c4_group<0>(v, s.base, A, cg);
-      else if (k == 1) c4_group<1>(v, s.base, A, cg);
-      else if (k == 2) c4_group<2>(v, s.base, A, cg);
-      else c4_group<3>(v, s.base, A, cg);
+      if (k == 0) c4_group<0>(v, A, cg);
+      else if (k == 1) c4_group<1>(v, A, cg);
+      else if (k == 2) c4_group<2>(v, A, cg);
+      else c4_group<3>(v, A, cg);
     }
     // o is now the address of combo gray4(15) = 8; walk back in the same order to store
 #pragma unroll
@@ -709,7 +728,7 @@ __device__ __forceinline__ void stage_c4(const Stage<float, float4> &s, const Pa
   if ((int)tid < ng) {
     const GroupDesc &d = s.gs[tid];
     C4Group r;
-    r.lutoff = (uint32_t)(reinterpret_cast<const unsigned char *>(s.lut + d.lut) - s.base);
+    r.lutoff = smem_u32(s.lut + d.lut);   // absolute shared address, aligned to the group's table size
     r.g01 = ((uint32_t)d.bccode[1] << 4) | ((uint32_t)d.bccode[2] << 20);
     r.g23 = ((uint32_t)d.bccode[4] << 4) | ((uint32_t)d.bccode[8] << 20);
     r.pad = 0;
@@ -785,18 +804,20 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
   }
 }
 
-// The same pass loop on the canonical 4-dimensional fast path (complex64, 12- and
+// The pass loop of the canonical 4-dimensional fast path (complex64, 12- and
 // 13-qubit tiles), as a kernel of its own so that its registers are allocated
-// for this path alone.
+// for this path alone.  (A variant with two tile buffers per CTA, at three CTAs
+// per SM, measured slower than one buffer at four CTAs per SM.)
 template <bool STREAM, int TT>
 __global__ void __launch_bounds__(NT, 4)
     k_sweep_c4(float *psi, int n, PassDesc pd, const GroupDesc *groups, const BlockDesc *blocks, const float2 *lut,
                unsigned *fault) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
-  const SmemLayout L = smem_layout(sizeof(float2), pd, 1, c4_extra_bytes(ng, nb), sizeof(float4),
-                                   sizeof(float4) << R_MAX_ROT);
-  const Stage<float, float4> st = stage_pass<float, float4>(smem, pd, L, groups, blocks, lut);
+  constexpr size_t LA = sizeof(float4) << R_MAX_ROT;
+  const SmemLayout L = smem_layout(sizeof(float2), pd, 1, c4_extra_bytes(ng, nb), sizeof(float4), LA, LA);
+  const Stage<float, float4> st =
+      stage_pass<float, float4>(smem, pd, L, groups, blocks, lut, abs_align_shift(smem, L.lut, LA));
   float2 *tile = reinterpret_cast<float2 *>(smem + L.tiles);
   __syncthreads();
   unsigned char *thr;
@@ -821,12 +842,12 @@ __global__ void __launch_bounds__(NT, 4)
     }
     for (int b = 0; b < nb; ++b) {
       sweep_block_c4<BlockShape<TT, 4>::J>(tile, st.bs[b], b, st, thr, cgs, btab);
-      __syncthreads();
+      if (b + 1 < nb) __syncthreads();
     }
-    fence_proxy_async();
+    fence_proxy_async();   // this thread's tile writes -> visible to the bulk store
     __syncthreads();
     bulk_store_tile(psi, base, st, tile);
-    bulk_wait_read();
+    bulk_wait_read();      // the tile may be overwritten once every store has read it
     __syncthreads();
   }
   bulk_wait_all();
@@ -1086,7 +1107,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *
 // combos of a coset and a group's LUT entries are walked in Gray-code order.
 
 struct alignas(16) EGroup {
-  uint32_t lutoff;   // byte offset of the group's LUT from the start of shared memory
+  uint32_t lutoff;   // shared-window address of the group's LUT (a multiple of its size)
   uint32_t g01;      // pair generators of block dimensions 0 and 1 (u16 each, already << 3)
   uint32_t g2;       // ... of dimension 2
   uint32_t kind_a;   // kind | (a << 8)
@@ -1111,14 +1132,14 @@ __device__ __forceinline__ float f2_lo_plus_hi(unsigned long long v) {
 
 // Pairs (c, c ^ X) of one REAL group over the thread's J cosets: sum of R (x_c x_p + y_c y_p).
 template <int D, int J, int X>
-__device__ __forceinline__ float efast_pairs(const unsigned long long (&v)[J][1 << D], const unsigned char *base,
-                                             uint32_t A, const uint8_t *bj, const EGroup &e) {
+__device__ __forceinline__ float efast_pairs(const unsigned long long (&v)[J][1 << D], uint32_t A, const uint8_t *bj,
+                                             const EGroup &e) {
   constexpr int HB = hbit(X);
   constexpr int P = 1 << (D - 1);
   uint32_t G[D > 1 ? D - 1 : 1];
 #pragma unroll
   for (int i = 0; i < D - 1; ++i) G[i] = egen(e, free_bit(HB, i));
-  unsigned long long acc = 0ull;
+  unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};   // independent chains
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     uint32_t a = A ^ ((uint32_t)bj[j] << 3);
@@ -1126,21 +1147,22 @@ __device__ __forceinline__ float efast_pairs(const unsigned long long (&v)[J][1 
     for (int t = 0; t < P; ++t) {
       const int p = t ^ (t >> 1);
       const int c = deposit_free(HB, p);
-      const unsigned long long rr = *reinterpret_cast<const unsigned long long *>(base + a);
-      acc = f2_fma(rr, f2_mul(v[j][c], v[j][c ^ X]), acc);
+      const unsigned long long rr = lds_b64(a);
+      unsigned long long &ak = acc[(j * P + t) & 3];
+      ak = f2_fma(rr, f2_mul(v[j][c], v[j][c ^ X]), ak);
       if (t + 1 < P) a ^= G[ctz_c(t + 1)];
     }
   }
-  return f2_lo_plus_hi(acc);
+  return (f2_lo_plus_hi(acc[0]) + f2_lo_plus_hi(acc[1])) + (f2_lo_plus_hi(acc[2]) + f2_lo_plus_hi(acc[3]));
 }
 
 template <int D, int J>
-__device__ __forceinline__ float efast_switch(int x, const unsigned long long (&v)[J][1 << D], const unsigned char *base,
-                                              uint32_t A, const uint8_t *bj, const EGroup &e) {
+__device__ __forceinline__ float efast_switch(int x, const unsigned long long (&v)[J][1 << D], uint32_t A,
+                                              const uint8_t *bj, const EGroup &e) {
   switch (x) {
 #define Q2_FC(X) \
   case X:        \
-    if constexpr (X < (1 << D)) return efast_pairs<D, J, X>(v, base, A, bj, e); \
+    if constexpr (X < (1 << D)) return efast_pairs<D, J, X>(v, A, bj, e); \
     break;
     Q2_FC(1) Q2_FC(2) Q2_FC(3) Q2_FC(4) Q2_FC(5) Q2_FC(6) Q2_FC(7)
 #undef Q2_FC
@@ -1149,9 +1171,21 @@ __device__ __forceinline__ float efast_switch(int x, const unsigned long long (&
   return 0.f;
 }
 
+// Issues the next tile's copy into the tile buffer once every thread holds its
+// amplitudes of the last block of a tile in registers (the tile is read only).
+struct EPrefetch {
+  bool now;           // this is the tile's last block
+  bool has_next;      // there is a next tile for this CTA
+  uint64_t next_base;
+  const float *psi;
+  float2 *tile;
+  uint64_t *bar;
+};
+
 template <int D, int J>
 __device__ __forceinline__ void expect_block_fast(const float2 *tile, const BlockDesc &B, const Stage<float> &s,
-                                                  const EGroup *egs, Kahan<float> &acc, bool norm, Kahan<float> &acc_n) {
+                                                  const EGroup *egs, Kahan<float> &acc, bool norm, Kahan<float> &acc_n,
+                                                  const EPrefetch &pf) {
   constexpr int N = 1 << D;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t bt = tid;
@@ -1171,13 +1205,17 @@ __device__ __forceinline__ void expect_block_fast(const float2 *tile, const Bloc
       if (t + 1 < N) o ^= W[ctz_c(t + 1)];
     }
   }
+  if (pf.now) {
+    __syncthreads();   // every thread's reads of the tile are done
+    if (pf.has_next) bulk_load_tile(pf.psi, pf.next_base, s, pf.tile, pf.bar);
+  }
   if (norm) {   // every amplitude of the tile is in exactly one coset of this block
-    unsigned long long n2 = 0ull;
+    unsigned long long n2[2] = {0ull, 0ull};
 #pragma unroll
     for (int j = 0; j < J; ++j)
 #pragma unroll
-      for (int c = 0; c < N; ++c) n2 = f2_fma(v[j][c], v[j][c], n2);
-    acc_n.add(f2_lo_plus_hi(n2));
+      for (int c = 0; c < N; ++c) n2[c & 1] = f2_fma(v[j][c], v[j][c], n2[c & 1]);
+    acc_n.add(f2_lo_plus_hi(n2[0]) + f2_lo_plus_hi(n2[1]));
   }
 #pragma unroll 1
   for (int gi = B.g_begin; gi < B.g_end; ++gi) {
@@ -1188,21 +1226,22 @@ __device__ __forceinline__ void expect_block_fast(const float2 *tile, const Bloc
     const int kind = (int)(e.kind_a & 0xffu);
     float sum;
     if (kind == KIND_DIAG) {
-      unsigned long long a2 = 0ull;
+      unsigned long long a2[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         uint32_t a = A ^ ((uint32_t)g.bjcode[j] << 3);
 #pragma unroll
         for (int t = 0; t < N; ++t) {
           const int c = t ^ (t >> 1);
-          const unsigned long long rr = *reinterpret_cast<const unsigned long long *>(s.base + a);
-          a2 = f2_fma(rr, f2_mul(v[j][c], v[j][c]), a2);
+          const unsigned long long rr = lds_b64(a);
+          unsigned long long &ak = a2[(j * N + t) & 3];
+          ak = f2_fma(rr, f2_mul(v[j][c], v[j][c]), ak);
           if (t + 1 < N) a ^= egen(e, ctz_c(t + 1));
         }
       }
-      sum = f2_lo_plus_hi(a2);
+      sum = (f2_lo_plus_hi(a2[0]) + f2_lo_plus_hi(a2[1])) + (f2_lo_plus_hi(a2[2]) + f2_lo_plus_hi(a2[3]));
     } else {
-      sum = 2.f * efast_switch<D, J>((int)(e.kind_a >> 8), v, s.base, A, g.bjcode, e);
+      sum = 2.f * efast_switch<D, J>((int)(e.kind_a >> 8), v, A, g.bjcode, e);
     }
     acc.add(sum);
   }
@@ -1211,11 +1250,11 @@ __device__ __forceinline__ void expect_block_fast(const float2 *tile, const Bloc
 template <int TT>
 __device__ __forceinline__ void expect_block_fast_any(const float2 *tile, const BlockDesc &B, const Stage<float> &s,
                                                       const EGroup *egs, Kahan<float> &acc, bool norm,
-                                                      Kahan<float> &acc_n) {
+                                                      Kahan<float> &acc_n, const EPrefetch &pf) {
   switch (B.d) {
-    case 1: expect_block_fast<1, BlockShape<TT, 1>::J>(tile, B, s, egs, acc, norm, acc_n); break;
-    case 2: expect_block_fast<2, BlockShape<TT, 2>::J>(tile, B, s, egs, acc, norm, acc_n); break;
-    default: expect_block_fast<3, BlockShape<TT, 3>::J>(tile, B, s, egs, acc, norm, acc_n); break;
+    case 1: expect_block_fast<1, BlockShape<TT, 1>::J>(tile, B, s, egs, acc, norm, acc_n, pf); break;
+    case 2: expect_block_fast<2, BlockShape<TT, 2>::J>(tile, B, s, egs, acc, norm, acc_n, pf); break;
+    default: expect_block_fast<3, BlockShape<TT, 3>::J>(tile, B, s, egs, acc, norm, acc_n, pf); break;
   }
 }
 
@@ -1225,9 +1264,9 @@ __global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, 
                                                        int first_pass, unsigned *fault) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
-  const SmemLayout L = smem_layout(sizeof(float2), pd, 1, efast_extra_bytes(ng), sizeof(float2),
-                                   sizeof(float2) << R_MAX);
-  const Stage<float> st = stage_pass<float>(smem, pd, L, groups, blocks, lut);
+  constexpr size_t LA = sizeof(float2) << R_MAX;
+  const SmemLayout L = smem_layout(sizeof(float2), pd, 1, efast_extra_bytes(ng), sizeof(float2), LA, LA);
+  const Stage<float> st = stage_pass<float>(smem, pd, L, groups, blocks, lut, abs_align_shift(smem, L.lut, LA));
   float2 *tile = reinterpret_cast<float2 *>(smem + L.tiles);
   double *red = reinterpret_cast<double *>(smem + L.extra);
   EGroup *egs = reinterpret_cast<EGroup *>(red + NT / 32);
@@ -1235,7 +1274,7 @@ __global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, 
   if ((int)threadIdx.x < ng) {
     const GroupDesc &d = st.gs[threadIdx.x];
     EGroup r;
-    r.lutoff = (uint32_t)(reinterpret_cast<const unsigned char *>(st.lut + d.lut) - st.base);
+    r.lutoff = smem_u32(st.lut + d.lut);   // absolute shared address, aligned to the group's table size
     r.g01 = ((uint32_t)d.bccode[1] << 3) | ((uint32_t)d.bccode[2] << 19);
     r.g2 = (uint32_t)d.bccode[4] << 3;
     r.kind_a = (uint32_t)d.kind | ((uint32_t)d.a << 8);
@@ -1248,8 +1287,9 @@ __global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, 
   __syncthreads();
   uint32_t parity = 0;
   TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
-    bulk_load_tile(psi, tw.base, st, tile, &bar);
+  if (blockIdx.x < ntiles) bulk_load_tile(psi, tw.base, st, tile, &bar);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    tw.next();   // tw.base: the next tile of this CTA
     tile_codes(st, ng, t);
     const bool ok = mbar_wait(&bar, parity, fault);
     parity ^= 1u;
@@ -1257,8 +1297,12 @@ __global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, 
       mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
       break;
     }
-    for (int b = 0; b < nb; ++b) expect_block_fast_any<TT>(tile, st.bs[b], st, egs, acc_e, first_pass && b == 0, acc_n);
-    __syncthreads();
+    EPrefetch pf{false, t + gridDim.x < ntiles, tw.base, psi, tile, &bar};
+    for (int b = 0; b < nb; ++b) {
+      pf.now = b == nb - 1;
+      expect_block_fast_any<TT>(tile, st.bs[b], st, egs, acc_e, first_pass && b == 0, acc_n, pf);
+    }
+    __syncthreads();   // the tile codes of this tile are read by the last block's groups
   }
   const double e = block_sum(acc_e.value(), red);
   const double nn = block_sum(acc_n.value(), red);
@@ -2254,15 +2298,15 @@ cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *gro
     if (c4 && (pd.T == 12 || pd.T == 13) && pd.g_end - pd.g_begin <= C4_MAX_GROUPS) {
       const size_t smem =
           smem_layout(sizeof(C2), pd, nvec, c4_extra_bytes(pd.g_end - pd.g_begin, pd.b_end - pd.b_begin), eb,
-                      (size_t)eb << R_MAX_ROT).total;
+                      (size_t)eb << R_MAX_ROT, (size_t)eb << R_MAX_ROT).total;
       const bool st_ = streaming(n, 2 * (int)sizeof(R));
       auto k = pd.T == 12 ? (st_ ? &k_sweep_c4<true, 12> : &k_sweep_c4<false, 12>)
                           : (st_ ? &k_sweep_c4<true, 13> : &k_sweep_c4<false, 13>);
       PassDesc wp = worst_pass(pd.T, pd.C);
       wp.g_end = C4_MAX_GROUPS;
       wp.b_end = C4_MAX_GROUPS / 4;
-      cudaError_t e = prepare(k, smem_layout(sizeof(C2), wp, nvec, c4_extra_bytes(C4_MAX_GROUPS, C4_MAX_GROUPS / 4), eb,
-                                             (size_t)eb << R_MAX_ROT).total);
+      cudaError_t e = prepare(k, smem_layout(sizeof(C2), wp, nvec, c4_extra_bytes(C4_MAX_GROUPS, C4_MAX_GROUPS / 4),
+                                             eb, (size_t)eb << R_MAX_ROT, (size_t)eb << R_MAX_ROT).total);
       if (e != cudaSuccess) return e;
       const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
       k<<<grid, NT, smem, st>>>(reinterpret_cast<float *>(psi), n, pd, groups, blocks,
@@ -2299,13 +2343,13 @@ cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDe
   if constexpr (sizeof(R) == 4) {
     if (lean && (pd.T == 12 || pd.T == 13)) {
       const int ng = pd.g_end - pd.g_begin;
-      const size_t smem =
-          smem_layout(sizeof(C2), pd, nvec, efast_extra_bytes(ng), sizeof(C2), sizeof(C2) << R_MAX).total;
+      const size_t smem = smem_layout(sizeof(C2), pd, nvec, efast_extra_bytes(ng), sizeof(C2), sizeof(C2) << R_MAX,
+                                      sizeof(C2) << R_MAX).total;
       const bool st_ = streaming(n, 2 * (int)sizeof(R));
       auto k = pd.T == 12 ? (st_ ? &k_expect_fast<true, 12> : &k_expect_fast<false, 12>)
                           : (st_ ? &k_expect_fast<true, 13> : &k_expect_fast<false, 13>);
-      cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, efast_extra_bytes(G_STAGE), sizeof(C2),
-                                            sizeof(C2) << R_MAX, ham_lut_max<R>()));
+      cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, nvec, efast_extra_bytes(G_STAGE) + (sizeof(C2) << R_MAX),
+                                            sizeof(C2), sizeof(C2) << R_MAX, ham_lut_max<R>()));
       if (e != cudaSuccess) return e;
       k<<<grid, NT, smem, st>>>(reinterpret_cast<const float *>(psi), n, pd, groups, blocks,
                                 reinterpret_cast<const float2 *>(lut), partial, first ? 1 : 0, fault);
