@@ -623,6 +623,7 @@ def config5(args, local):
         res["offered_fraction_of_capacity"] = frac
         log(f"[config5] {frac:.1f} x capacity: {res['completed']}/{res['requests']} in {res['wall_s']:.1f}s, "
             f"{res['evals_per_s']:.2f} evals/s, p50 {res['p50_latency_s']:.3f}s p99 {res['p99_latency_s']:.3f}s")
+        log("[config5] " + json.dumps(res))
         rates.append(res)
     line = {"metric": "served_evals_per_s", "value": rates[-1]["evals_per_s"], "unit": "evals/s",
             "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32",

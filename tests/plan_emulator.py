@@ -447,3 +447,106 @@ def sweep_c4(psi, n, passes, groups, blocks, lut, NT, lut_base=5 * 1024):
                     tile[:, addr[c] >> 3] = v[c]
         psi[idx] = tile
     return psi
+
+
+def expectation_chunked(psi, n, passes, groups, blocks, lut, NT, jc):
+    """(sum_t c_t <P_t>, <psi|psi>) walking the Hamiltonian schedule as the general
+    expectation kernel does: a thread's J cosets of a block are taken in chunks of jc
+    (jc * 2^d amplitudes in registers); within a chunk, coset j0 + j uses code
+    tilecode ^ blane ^ bwarp ^ bjcode[j0 + j] ^ bccode[c]; every group of the block is
+    walked once per chunk.  Any jc in 1..J that divides J gives the same sum."""
+    e = 0.0
+    for pd in passes:
+        T = int(pd["T"])
+        idx = tile_index(n, pd)
+        tile = psi[idx]
+        ntiles = tile.shape[0]
+        g0 = int(pd["g_begin"])
+        for bi in range(int(pd["b_begin"]), int(pd["b_end"])):
+            b = blocks[bi]
+            d, J, nthr, l, lane, warp = _block_layout(b, T, NT)
+            step = min(jc, J)
+            assert J % step == 0
+            for j0 in range(0, J, step):
+                amps = tile[:, l[:, j0:j0 + step, :]]           # [t, tid, j, c]
+                for gk in range(int(b["g_begin"]), int(b["g_end"])):
+                    g = groups[g0 + gk]
+                    th = g["blane"][lane].astype(np.int64) ^ g["bwarp"][warp].astype(np.int64)
+                    cb = _tilecode(g, T, ntiles)[:, None, None] ^ th[None, :, None]
+                    cj = cb ^ g["bjcode"][j0:j0 + step].astype(np.int64)[None, None, :]
+                    code = cj[..., None] ^ g["bccode"][:1 << d].astype(np.int64)[None, None, None, :]
+                    rq = lut[int(g["lut"]) + code]
+                    if int(g["kind"]) == DIAG:
+                        e += float(np.sum(rq[..., 0] * np.abs(amps) ** 2))
+                        continue
+                    ci, cjp = _pair_combos(int(g["a"]), d)
+                    w = np.conj(amps[..., ci]) * amps[..., cjp]
+                    e += float(np.sum(2 * (rq[..., ci, 0] * w.real + rq[..., ci, 1] * w.imag)))
+    return e, float(np.vdot(psi, psi).real)
+
+
+def expectation_lean(psi, n, passes, groups, blocks, lut, NT, lut_base=7 * 2048):
+    """The lean expectation path's exact address arithmetic (REAL and DIAG groups, blocks of
+    d <= 3): amplitude byte offsets (8 bytes) walked in Gray-code order from
+    (base(tid) ^ uj[j]) << 3 over W_i = comb[1 << i] << 3; per group the LUT byte address
+    A = lutaddr | (tilecode ^ blane ^ bwarp) << 3, per coset A ^ bjcode[j] << 3, then a Gray
+    walk over the pair (or, for DIAG, combo) bits with generators bccode[1 << i] << 3;
+    the group's LUT starts at a multiple of its size from a 2 KiB-aligned `lut_base`."""
+    e = 0.0
+    for pd in passes:
+        T = int(pd["T"])
+        idx = tile_index(n, pd)
+        tile = psi[idx]
+        ntiles = tile.shape[0]
+        g0 = int(pd["g_begin"])
+        tid = np.arange(NT, dtype=np.int64)
+        lane, warp = tid % 32, tid // 32
+        for bi in range(int(pd["b_begin"]), int(pd["b_end"])):
+            b = blocks[bi]
+            d = int(b["d"])
+            assert d <= 3
+            N, J = 1 << d, (1 << (T - d)) // NT
+            bt = tid.astype(np.uint64)
+            for i in range(d):
+                bt = _insert0(bt, int(b["piv"][i]))
+            bt = bt.astype(np.int64)
+            W = [int(b["comb"][1 << i]) << 3 for i in range(d)]
+            v = {}
+            for j in range(J):
+                o = (bt ^ int(b["uj"][j])) << 3
+                for t in range(N):
+                    v[j, _gray(t)] = tile[:, o >> 3]
+                    if t + 1 < N:
+                        o = o ^ W[_ctz(t + 1)]
+            for gk in range(int(b["g_begin"]), int(b["g_end"])):
+                g = groups[g0 + gk]
+                kind = int(g["kind"])
+                assert kind in (DIAG, REAL)
+                lutaddr = lut_base + (int(g["lut"]) - int(pd["lut_begin"])) * 8
+                assert lutaddr % (8 << int(g["r"])) == 0
+                th = g["blane"][lane].astype(np.int64) ^ g["bwarp"][warp].astype(np.int64)
+                A = lutaddr | ((_tilecode(g, T, ntiles)[:, None] ^ th[None, :]) << 3)
+                gens = [int(g["bccode"][1 << i]) << 3 for i in range(d)]
+                s = 0.0
+                for j in range(J):
+                    a = A ^ (int(g["bjcode"][j]) << 3)
+                    if kind == DIAG:
+                        for t in range(N):
+                            r = lut[(a - lut_base) // 8 + int(pd["lut_begin"]), 0]
+                            s += float(np.sum(r * np.abs(v[j, _gray(t)]) ** 2))
+                            if t + 1 < N:
+                                a = a ^ gens[_ctz(t + 1)]
+                    else:
+                        x = int(g["a"])
+                        hb = x.bit_length() - 1
+                        free = [i for i in range(d) if i != hb]
+                        for t in range(N // 2):
+                            p = _gray(t)
+                            c = sum(((p >> i) & 1) << free[i] for i in range(d - 1))
+                            r = lut[(a - lut_base) // 8 + int(pd["lut_begin"]), 0]
+                            w = np.conj(v[j, c]) * v[j, c ^ x]
+                            s += 2 * float(np.sum(r * w.real))
+                            if t + 1 < N // 2:
+                                a = a ^ gens[free[_ctz(t + 1)]]
+                e += s
+    return e, float(np.vdot(psi, psi).real)

@@ -343,3 +343,31 @@ def test_sweep_fast_path_walk_matches_oracle(lib, n, T, seed):
     ref = sv.apply_rotations(psi0, ans.x, ans.z, phi)
     got = emu.sweep_c4(psi0, n, passes, groups, blocks, lut, lib.q2_debug_threads_per_cta())
     assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("n,T,C", [(14, 13, 4), (15, 12, 4), (13, 11, 4)])
+def test_expectation_chunk_shapes_and_lean_walk_match_oracle(lib, n, T, C):
+    """The general expectation kernel takes each block's cosets in chunks; every chunk size
+    the template admits for every block dimension (d = 1, 2, 3; chunks of 1, 2, 4, ... cosets
+    up to J) walks bjcode[j0 + j] the same way and gives the oracle's energy, so the chunk
+    indexing is not a source of error.  The lean path's Gray-code address walks give it too."""
+    from synth.workloads import sweep32
+    w = sweep32(seed=n, n=n, n_elec=n // 2, n_rot=8, min_terms=900)
+    passes, groups, blocks, lut = emu.ham_plan(lib, n, w.ham.x, w.ham.z, w.ham.c, T, C)
+    rng = np.random.default_rng(n)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi /= np.linalg.norm(psi)
+    e_ref = sv.expectation(psi, w.ham.x, w.ham.z, w.ham.c)
+    NT = lib.q2_debug_threads_per_cta()
+    dims = {int(b["d"]) for b in blocks}
+    assert {1, 3} <= dims
+    J_min = min((1 << (T - int(b["d"]))) // NT for b in blocks)
+    for jc in [1, 2, 4, 8, 16]:
+        if jc > J_min and jc > 1:
+            break
+        e, nrm = emu.expectation_chunked(psi, n, passes, groups, blocks, lut, NT, jc)
+        assert abs(e - e_ref) < 1e-10, jc
+        assert abs(nrm - 1) < 1e-12
+    if all(int(g["kind"]) in (emu.DIAG, emu.REAL) for g in groups) and all(int(b["d"]) <= 3 for b in blocks):
+        e, _ = emu.expectation_lean(psi, n, passes, groups, blocks, lut, NT)
+        assert abs(e - e_ref) < 1e-10
