@@ -1111,10 +1111,26 @@ struct alignas(16) EGroup {
   uint32_t g01;      // pair generators of block dimensions 0 and 1 (u16 each, already << 3)
   uint32_t g2;       // ... of dimension 2
   uint32_t kind_a;   // kind | (a << 8)
+  uint32_t bj[2];    // coset codes bjcode[0..3] << 3 as u16 (cosets of 3-dimensional blocks)
+  uint32_t pad[2];
 };
 
 __host__ __device__ inline size_t efast_extra_bytes(int ng) {
   return sizeof(double) * (NT / 32) + sizeof(EGroup) * (size_t)ng;
+}
+
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// XOR of coset j's code (<< 3) into a LUT address: from the staged record for J <= 4,
+// from the group descriptor otherwise.
+template <int J>
+__device__ __forceinline__ uint32_t coset_code3(const EGroup &e, const uint8_t *bj, int j) {
+  if constexpr (J <= 4) return (j & 1) ? (e.bj[j >> 1] >> 16) : (e.bj[j >> 1] & 0xffffu);
+  else return (uint32_t)bj[j] << 3;
 }
 
 __device__ __forceinline__ uint32_t egen(const EGroup &g, int i) {
@@ -1142,7 +1158,7 @@ __device__ __forceinline__ float efast_pairs(const unsigned long long (&v)[J][1 
   unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};   // independent chains
 #pragma unroll
   for (int j = 0; j < J; ++j) {
-    uint32_t a = A ^ ((uint32_t)bj[j] << 3);
+    uint32_t a = A ^ coset_code3<J>(e, bj, j);
 #pragma unroll
     for (int t = 0; t < P; ++t) {
       const int p = t ^ (t >> 1);
@@ -1153,7 +1169,7 @@ __device__ __forceinline__ float efast_pairs(const unsigned long long (&v)[J][1 
       if (t + 1 < P) a ^= G[ctz_c(t + 1)];
     }
   }
-  return (f2_lo_plus_hi(acc[0]) + f2_lo_plus_hi(acc[1])) + (f2_lo_plus_hi(acc[2]) + f2_lo_plus_hi(acc[3]));
+  return f2_lo_plus_hi(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])));
 }
 
 template <int D, int J>
@@ -1229,7 +1245,7 @@ __device__ __forceinline__ void expect_block_fast(const float2 *tile, const Bloc
       unsigned long long a2[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        uint32_t a = A ^ ((uint32_t)g.bjcode[j] << 3);
+        uint32_t a = A ^ coset_code3<J>(e, g.bjcode, j);
 #pragma unroll
         for (int t = 0; t < N; ++t) {
           const int c = t ^ (t >> 1);
@@ -1239,7 +1255,7 @@ __device__ __forceinline__ void expect_block_fast(const float2 *tile, const Bloc
           if (t + 1 < N) a ^= egen(e, ctz_c(t + 1));
         }
       }
-      sum = (f2_lo_plus_hi(a2[0]) + f2_lo_plus_hi(a2[1])) + (f2_lo_plus_hi(a2[2]) + f2_lo_plus_hi(a2[3]));
+      sum = f2_lo_plus_hi(f2_add(f2_add(a2[0], a2[1]), f2_add(a2[2], a2[3])));
     } else {
       sum = 2.f * efast_switch<D, J>((int)(e.kind_a >> 8), v, A, g.bjcode, e);
     }
@@ -1278,6 +1294,9 @@ __global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, 
     r.g01 = ((uint32_t)d.bccode[1] << 3) | ((uint32_t)d.bccode[2] << 19);
     r.g2 = (uint32_t)d.bccode[4] << 3;
     r.kind_a = (uint32_t)d.kind | ((uint32_t)d.a << 8);
+    r.bj[0] = ((uint32_t)d.bjcode[0] << 3) | ((uint32_t)d.bjcode[1] << 19);
+    r.bj[1] = ((uint32_t)d.bjcode[2] << 3) | ((uint32_t)d.bjcode[3] << 19);
+    r.pad[0] = r.pad[1] = 0;
     egs[threadIdx.x] = r;
   }
   const uint64_t ntiles = 1ull << (n - pd.T);
