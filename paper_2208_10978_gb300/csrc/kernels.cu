@@ -287,6 +287,9 @@ __device__ __forceinline__ ulonglong2 lds_b128(uint32_t addr) {
   asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
   return v;
 }
+__device__ __forceinline__ void sts_b64(uint32_t addr, unsigned long long v) {
+  asm volatile("st.shared.b64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -675,7 +678,7 @@ template <int J>
 __device__ __forceinline__ void sweep_block_c4(float2 *tile, const BlockDesc &B, int b, const Stage<float, float4> &s,
                                                const unsigned char *thr, const C4Group *cgs, const uint16_t *btab) {
   const uint32_t tid = threadIdx.x;
-  unsigned char *tb = reinterpret_cast<unsigned char *>(tile);
+  const uint32_t tb = smem_u32(tile);   // shared-window address of the tile
   const uint32_t W0 = (uint32_t)B.comb[1] << 3, W1 = (uint32_t)B.comb[2] << 3, W2 = (uint32_t)B.comb[4] << 3,
                  W3 = (uint32_t)B.comb[8] << 3;
   const int gb = B.g_begin;
@@ -686,7 +689,7 @@ __device__ __forceinline__ void sweep_block_c4(float2 *tile, const BlockDesc &B,
     uint32_t o = (bt ^ B.uj[j]) << 3;
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
-      v[gray4(t)] = *reinterpret_cast<const unsigned long long *>(tb + o);
+      v[gray4(t)] = lds_b64(tb + o);
       if (t < 15) {
         const int f = gray_flip4(t);
         o ^= f == 0 ? W0 : f == 1 ? W1 : f == 2 ? W2 : W3;
@@ -707,7 +710,7 @@ __device__ __forceinline__ void sweep_block_c4(float2 *tile, const BlockDesc &B,
     // o is now the address of combo gray4(15) = 8; walk back in the same order to store
 #pragma unroll
     for (int t = 15; t >= 0; --t) {
-      *reinterpret_cast<unsigned long long *>(tb + o) = v[gray4(t)];
+      sts_b64(tb + o, v[gray4(t)]);
       if (t > 0) {
         const int f = gray_flip4(t - 1);
         o ^= f == 0 ? W0 : f == 1 ? W1 : f == 2 ? W2 : W3;
@@ -1210,14 +1213,14 @@ __device__ __forceinline__ void expect_block_fast(const float2 *tile, const Bloc
   uint32_t W[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) W[i] = (uint32_t)B.comb[1 << i] << 3;
-  const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile);
+  const uint32_t tb = smem_u32(tile);   // shared-window address of the tile
   unsigned long long v[J][N];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     uint32_t o = (bt ^ B.uj[j]) << 3;
 #pragma unroll
     for (int t = 0; t < N; ++t) {
-      v[j][t ^ (t >> 1)] = *reinterpret_cast<const unsigned long long *>(tb + o);
+      v[j][t ^ (t >> 1)] = lds_b64(tb + o);
       if (t + 1 < N) o ^= W[ctz_c(t + 1)];
     }
   }
@@ -2040,6 +2043,7 @@ __global__ void __launch_bounds__(NT, 2) k_reverse_blk(float *psi, float *lam, i
   float *wst = reinterpret_cast<float *>(smem + rs.w_off);
   rs.wacc = reinterpret_cast<double *>(smem + rs.w_off + align16(sizeof(float) * (size_t)pd.lut_count));
   for (int i = threadIdx.x; i < (NT / 32) * G_STAGE; i += NT) rs.wacc[i] = 0.0;
+  __syncthreads();   // group descriptors are staged by other warps' 16-byte copies
   for (int g = threadIdx.x; g < ng; g += NT) {   // weights beside the LUT entries of each group
     const GroupDesc &d = st.gs[g];
     const uint32_t rel = d.lut - (uint32_t)pd.lut_begin;

@@ -127,6 +127,7 @@ class Server:
         self._small = []
         self._small_cv = threading.Condition()
         self._stop = False
+        self._broken = ""          # set when a loop died: new requests fail at once
         self._threads = [threading.Thread(target=self._admit_loop, daemon=True),
                          threading.Thread(target=self._batch_loop, daemon=True)]
         self._threads += [threading.Thread(target=self._worker_loop, daemon=True) for _ in range(n_streams)]
@@ -163,6 +164,10 @@ class Server:
         with self._lock:
             if self._closed:
                 raise RuntimeError("server is closed")
+            if self._broken:
+                fut.set_result(Result(job.rid, Q2_ERR_INVALID, t_submit=job.t_submit, t_done=self.now(),
+                                      error="server loop stopped: " + self._broken))
+                return fut
             self._jobs[job.rid] = job
             st = self._L.q2_server_submit(self._core, job.rid, nbytes, pid, tbytes, job.t_submit)
             if st != Q2_OK:
@@ -279,6 +284,8 @@ class Server:
 
     def _fail_all(self, status, error):
         with self._lock:
+            if not self._broken and status != Q2_OK and "server closed" not in error:
+                self._broken = error
             jobs = list(self._jobs.values())
         for j in jobs:
             if not j.future.done():

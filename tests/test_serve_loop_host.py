@@ -125,3 +125,24 @@ def test_unused_problem_tables_are_released_lru(problems):
     assert all(r.status == q2.Q2_OK for r in results)
     assert st["evictions"] >= 8 and st["resident_problems"] <= 2
     assert st["high_water_bytes"] <= budget and st["table_bytes"] <= 2.5 * tables
+
+
+def test_a_dead_loop_fails_new_requests_at_once(problems):
+    """When a loop dies on an error it cannot report per request (for instance a sticky device
+    error), every pending request is resolved with that error and later requests fail at once
+    instead of waiting in the queue."""
+
+    class Dying(HostServer):
+        def _run_large(self, job, stream, ws):
+            raise RuntimeError("device context lost")
+
+    srv = Dying(budget_bytes=2**34, max_slots=4, n_streams=1)
+    p = problems[2]
+    try:
+        first = srv.submit(1, p, np.zeros(p.n_params), False).result(timeout=10)
+        assert first.status != q2.Q2_OK and "device context lost" in first.error
+        later = srv.submit(2, p, np.zeros(p.n_params), False).result(timeout=1)
+        assert later.status != q2.Q2_OK and "server loop stopped" in later.error
+    finally:
+        srv._threads = [t for t in srv._threads if t.is_alive()]
+        srv.close(timeout_s=10)
