@@ -4,8 +4,9 @@
 // tiles of one pass; each CTA brings a tile (2^(T-C) chunks of 2^C
 // contiguous amplitudes) into shared memory -- by bulk async copies counted
 // on an mbarrier for tiles of 2^9 amplitudes and more, by 16-byte loads
-// below that -- applies all groups of the pass there, and writes the tile
-// back (or only reduces it).  Tiles are cosets of the pass's local subspace
+// below that, and by per-thread 16-byte async copies in the two fast kernels
+// (k_sweep_c4, k_expect_fast) -- applies all groups of the pass there, and
+// writes the tile back (or only reduces it).  Tiles are cosets of the pass's local subspace
 // W (see q2_internal.h), so a pass touches every amplitude exactly once and
 // tiles never overlap.  The pass's offsets, group and block descriptors and
 // LUT are staged in shared memory once per CTA.
@@ -260,7 +261,9 @@ __device__ __forceinline__ void store_tile(R *dstg, uint64_t base, const Stage<R
 // results), and the CTA stops working on its tiles.  Kernels of calls that
 // return before their work completes (q2_apply_pauli_rotations,
 // q2_apply_hamiltonian) get no fault word and count into g_async_faults,
-// which only q2_async_status reads and clears.
+// which only q2_async_status reads and clears.  The two fast kernels use
+// per-thread copies instead (async_load_tile): their waits are hardware
+// dependency waits on the thread's own copies, like those of ordinary loads.
 
 __device__ unsigned int g_async_faults;
 
@@ -597,6 +600,33 @@ __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, co
   }
 }
 
+// Per-thread asynchronous tile copies (the two fast kernels).  A bulk copy is
+// one instruction per chunk whose operands differ from lane to lane, and ncu
+// counts about 2,000 instructions per CTA for the 256 chunk copies of a 2^12
+// tile each way; 16-byte cp.async copies, consecutive threads on consecutive
+// pieces, take 8 per thread and a hardware dependency wait (no poll).  Stores
+// go the plain way (store_tile), from shared memory through registers.
+template <typename R, typename E>
+__device__ __forceinline__ void async_load_tile(const R *src, uint64_t base, const Stage<R, E> &tc,
+                                                typename Vec2<R>::type *tile) {
+  using V = typename Vec16<R>::type;
+  constexpr int A = Vec16<R>::amps;
+  const uint32_t nv = tc.amps / A;
+  const uint32_t cm = (1u << tc.C) - 1u;
+  const V *g = reinterpret_cast<const V *>(src);
+  const uint32_t sb = smem_u32(tile);
+#pragma unroll 4
+  for (uint32_t v = threadIdx.x; v < nv; v += NT) {
+    const uint32_t l = v * A;
+    const uint64_t i = (base ^ tc.off[l >> tc.C]) | (l & cm);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + v * 16u), "l"((const void *)(g + i / A))
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Wait for this thread's asynchronous copies; the caller then syncs the CTA.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // ------------------------------------------------------------------ canonical 4-dimensional sweep blocks
 //
 // Fast path for passes whose register blocks are all canonical and 4-dimensional
@@ -611,6 +641,7 @@ __device__ __forceinline__ void sweep_block_any(typename Vec2<R>::type *tile, co
 // Per tile and group only the tile code is added.  Amplitudes are kept as packed
 // 64-bit (re, im) registers for the f32x2 instructions, and the combos of a coset
 // and the LUT entries of a group are walked in Gray-code order, one XOR per step.
+// Tiles come in by per-thread async copies and go out by plain streaming stores.
 
 constexpr int C4_MAX_GROUPS = 16;   // groups of a pass on this path (4 blocks)
 
@@ -813,8 +844,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 3)
 // per SM, measured slower than one buffer at four CTAs per SM.)
 template <bool STREAM, int TT>
 __global__ void __launch_bounds__(NT, 4)
-    k_sweep_c4(float *psi, int n, PassDesc pd, const GroupDesc *groups, const BlockDesc *blocks, const float2 *lut,
-               unsigned *fault) {
+    k_sweep_c4(float *psi, int n, PassDesc pd, const GroupDesc *groups, const BlockDesc *blocks, const float2 *lut) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   constexpr size_t LA = sizeof(float4) << R_MAX_ROT;
@@ -827,33 +857,24 @@ __global__ void __launch_bounds__(NT, 4)
   C4Group *cgs;
   uint16_t *btab;
   stage_c4(st, pd, smem + L.extra, &thr, &cgs, &btab);
-  __shared__ uint64_t bar;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
+  using V = typename Vec16<float>::type;
   const uint64_t ntiles = 1ull << (n - pd.T);
-  uint32_t parity = 0;
   TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
     const uint64_t base = tw.base;
-    bulk_load_tile(psi, base, st, tile, &bar);
+    async_load_tile(psi, base, st, tile);
     tile_codes(st, ng, t);
-    const bool ok = mbar_wait(&bar, parity, fault);
-    parity ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
-      break;
-    }
+    cp_async_wait_all();
+    __syncthreads();
     for (int b = 0; b < nb; ++b) {
       sweep_block_c4<BlockShape<TT, 4>::J>(tile, st.bs[b], b, st, thr, cgs, btab);
       if (b + 1 < nb) __syncthreads();
     }
-    fence_proxy_async();   // this thread's tile writes -> visible to the bulk store
     __syncthreads();
-    bulk_store_tile(psi, base, st, tile);
-    bulk_wait_read();      // the tile may be overwritten once every store has read it
-    __syncthreads();
+    store_tile<float, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
+    __syncthreads();   // every thread has read its pieces before the next tile lands
   }
-  bulk_wait_all();
 }
 
 // ------------------------------------------------------------------ reductions
@@ -1108,6 +1129,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_expect(const R *
 // compensated accumulator once.  Per group and pass the LUT byte offset and
 // the pair generators (bccode[1 << i] << 3) are staged once per CTA; the
 // combos of a coset and a group's LUT entries are walked in Gray-code order.
+// Tiles come in by per-thread async copies; the next tile's copy is issued as
+// soon as the last block of the current tile is in registers.
 
 struct alignas(16) EGroup {
   uint32_t lutoff;   // shared-window address of the group's LUT (a multiple of its size)
@@ -1198,7 +1221,6 @@ struct EPrefetch {
   uint64_t next_base;
   const float *psi;
   float2 *tile;
-  uint64_t *bar;
 };
 
 template <int D, int J>
@@ -1226,7 +1248,7 @@ __device__ __forceinline__ void expect_block_fast(const float2 *tile, const Bloc
   }
   if (pf.now) {
     __syncthreads();   // every thread's reads of the tile are done
-    if (pf.has_next) bulk_load_tile(pf.psi, pf.next_base, s, pf.tile, pf.bar);
+    if (pf.has_next) async_load_tile(pf.psi, pf.next_base, s, pf.tile);
   }
   if (norm) {   // every amplitude of the tile is in exactly one coset of this block
     unsigned long long n2[2] = {0ull, 0ull};
@@ -1280,7 +1302,7 @@ __device__ __forceinline__ void expect_block_fast_any(const float2 *tile, const 
 template <bool STREAM, int TT>
 __global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, PassDesc pd, const GroupDesc *groups,
                                                        const BlockDesc *blocks, const float2 *lut, double *partial,
-                                                       int first_pass, unsigned *fault) {
+                                                       int first_pass) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
   constexpr size_t LA = sizeof(float2) << R_MAX;
@@ -1304,22 +1326,15 @@ __global__ void __launch_bounds__(NT, 2) k_expect_fast(const float *psi, int n, 
   }
   const uint64_t ntiles = 1ull << (n - pd.T);
   Kahan<float> acc_e, acc_n;
-  __shared__ uint64_t bar;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
-  uint32_t parity = 0;
   TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
-  if (blockIdx.x < ntiles) bulk_load_tile(psi, tw.base, st, tile, &bar);
+  if (blockIdx.x < ntiles) async_load_tile(psi, tw.base, st, tile);
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     tw.next();   // tw.base: the next tile of this CTA
     tile_codes(st, ng, t);
-    const bool ok = mbar_wait(&bar, parity, fault);
-    parity ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
-      break;
-    }
-    EPrefetch pf{false, t + gridDim.x < ntiles, tw.base, psi, tile, &bar};
+    cp_async_wait_all();
+    __syncthreads();
+    EPrefetch pf{false, t + gridDim.x < ntiles, tw.base, psi, tile};
     for (int b = 0; b < nb; ++b) {
       pf.now = b == nb - 1;
       expect_block_fast_any<TT>(tile, st.bs[b], st, egs, acc_e, first_pass && b == 0, acc_n, pf);
@@ -2333,7 +2348,7 @@ cudaError_t launch_sweep(R *psi, int n, const PassDesc &pd, const GroupDesc *gro
       if (e != cudaSuccess) return e;
       const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
       k<<<grid, NT, smem, st>>>(reinterpret_cast<float *>(psi), n, pd, groups, blocks,
-                                reinterpret_cast<const float2 *>(lut), fault);
+                                reinterpret_cast<const float2 *>(lut));
       return cudaGetLastError();
     }
   }
@@ -2375,7 +2390,7 @@ cudaError_t launch_expect(const R *psi, int n, const PassDesc &pd, const GroupDe
                                             sizeof(C2), sizeof(C2) << R_MAX, ham_lut_max<R>()));
       if (e != cudaSuccess) return e;
       k<<<grid, NT, smem, st>>>(reinterpret_cast<const float *>(psi), n, pd, groups, blocks,
-                                reinterpret_cast<const float2 *>(lut), partial, first ? 1 : 0, fault);
+                                reinterpret_cast<const float2 *>(lut), partial, first ? 1 : 0);
       return cudaGetLastError();
     }
   }
