@@ -627,6 +627,42 @@ __device__ __forceinline__ void async_load_tile(const R *src, uint64_t base, con
 // Wait for this thread's asynchronous copies; the caller then syncs the CTA.
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Write tile `base` back and start the copy of tile `next` into the same shared
+// memory: each thread moves the 16-byte pieces it owns in both copies (pieces
+// tid, tid + NT, ...), so once a piece is in registers and stored, the thread
+// may refill it without waiting for the CTA.  Eight pieces per batch.
+template <int TT, bool STREAM, typename E>
+__device__ __forceinline__ void store_load_tile(float *psi, uint64_t base, uint64_t next, const Stage<float, E> &tc,
+                                                float2 *tile) {
+  using V = typename Vec16<float>::type;
+  constexpr int A = Vec16<float>::amps;
+  constexpr int PER = (1 << TT) / A / NT;   // pieces per thread
+  constexpr int BATCH = PER < 8 ? PER : 8;
+  const uint32_t cm = (1u << tc.C) - 1u;
+  V *g = reinterpret_cast<V *>(psi);
+  const V *tv = reinterpret_cast<const V *>(tile);
+  const uint32_t sb = smem_u32(tile);
+#pragma unroll
+  for (int k0 = 0; k0 < PER; k0 += BATCH) {
+    V buf[BATCH];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) buf[k] = tv[(k0 + k) * NT + threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const uint32_t v = (k0 + k) * NT + threadIdx.x, l = v * A;
+      st16<V, STREAM>(g + ((base ^ tc.off[l >> tc.C]) | (l & cm)) / A, buf[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const uint32_t v = (k0 + k) * NT + threadIdx.x, l = v * A;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + v * 16u),
+                   "l"((const void *)(g + ((next ^ tc.off[l >> tc.C]) | (l & cm)) / A))
+                   : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ canonical 4-dimensional sweep blocks
 //
 // Fast path for passes whose register blocks are all canonical and 4-dimensional
@@ -861,9 +897,10 @@ __global__ void __launch_bounds__(NT, 4)
   using V = typename Vec16<float>::type;
   const uint64_t ntiles = 1ull << (n - pd.T);
   TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
+  if (blockIdx.x < ntiles) async_load_tile(psi, tw.base, st, tile);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = tw.base;
-    async_load_tile(psi, base, st, tile);
+    tw.next();   // tw.base: the next tile of this CTA
     tile_codes(st, ng, t);
     cp_async_wait_all();
     __syncthreads();
@@ -871,9 +908,9 @@ __global__ void __launch_bounds__(NT, 4)
       sweep_block_c4<BlockShape<TT, 4>::J>(tile, st.bs[b], b, st, thr, cgs, btab);
       if (b + 1 < nb) __syncthreads();
     }
-    __syncthreads();
-    store_tile<float, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
-    __syncthreads();   // every thread has read its pieces before the next tile lands
+    __syncthreads();   // the tile is final and every group's tile code has been read
+    if (t + gridDim.x < ntiles) store_load_tile<TT, STREAM>(psi, base, tw.base, st, tile);
+    else store_tile<float, STREAM>(psi, base, st, reinterpret_cast<const V *>(tile));
   }
 }
 
