@@ -1660,53 +1660,34 @@ __device__ __forceinline__ void happly_block_any(const typename Vec2<R>::type *t
 template <typename R, int TT>
 __global__ void __launch_bounds__(NT, 2) k_happly_blk(const R *psi, R *lam, int n, PassDesc pd,
                                                       const GroupDesc *groups, const BlockDesc *blocks,
-                                                      const typename Vec2<R>::type *lut, int first_pass,
-                                                      unsigned *fault) {
+                                                      const typename Vec2<R>::type *lut, int first_pass) {
   using C2 = typename Vec2<R>::type;
+  using V = typename Vec16<R>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(sizeof(C2), pd, 2, 0, sizeof(C2), sizeof(C2) << R_MAX);
   const Stage<R> st = stage_pass<R>(smem, pd, L, groups, blocks, lut);
   C2 *tp = reinterpret_cast<C2 *>(smem + L.tiles);
   C2 *tl = tp + st.amps;
   const int ng = pd.g_end - pd.g_begin, nb = pd.b_end - pd.b_begin;
-  __shared__ uint64_t bar;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   const uint64_t ntiles = 1ull << (n - pd.T);
-  const uint32_t nch = 1u << (pd.T - pd.C);
-  const uint32_t bytes = (uint32_t)sizeof(C2) << pd.C;
-  uint32_t parity = 0;
   TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
     const uint64_t base = tw.base;
-    if (threadIdx.x == 0) mbar_expect_tx(&bar, (first_pass ? 1u : 2u) * bytes * nch);
-    for (uint32_t h = threadIdx.x; h < nch; h += NT) {
-      const uint64_t gi = base ^ st.off[h];
-      bulk_g2s(tp + (h << pd.C), reinterpret_cast<const C2 *>(psi) + gi, bytes, &bar);
-      if (!first_pass) bulk_g2s(tl + (h << pd.C), reinterpret_cast<const C2 *>(lam) + gi, bytes, &bar);
-    }
-    if (first_pass)
+    async_load_tile(psi, base, st, tp);
+    if (!first_pass) async_load_tile(lam, base, st, tl);
+    else
       for (uint32_t l = threadIdx.x; l < st.amps; l += NT) tl[l] = C2{0, 0};
     tile_codes(st, ng, t);
-    const bool ok = mbar_wait(&bar, parity, fault);
-    parity ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
-      break;
-    }
+    cp_async_wait_all();
+    __syncthreads();
     for (int b = 0; b < nb; ++b) {
       happly_block_any<R, TT>(tp, tl, st.bs[b], st);
       __syncthreads();
     }
-    fence_proxy_async();
-    __syncthreads();
-    for (uint32_t h = threadIdx.x; h < nch; h += NT)
-      bulk_s2g(reinterpret_cast<C2 *>(lam) + (base ^ st.off[h]), tl + (h << pd.C), bytes);
-    bulk_commit();
-    bulk_wait_read();
-    __syncthreads();
+    store_tile<R, false>(lam, base, st, reinterpret_cast<const V *>(tl));
+    __syncthreads();   // every thread has read its pieces before the next tiles land
   }
-  bulk_wait_all();
 }
 
 // Re<psi|lam> and <psi|psi>, per-CTA partials.
@@ -2081,8 +2062,7 @@ __host__ __device__ inline size_t rev_extra_bytes(int lut_count) {
 template <int TT>
 __global__ void __launch_bounds__(NT, 2) k_reverse_blk(float *psi, float *lam, int n, PassDesc pd,
                                                        const GroupDesc *groups, const BlockDesc *blocks,
-                                                       const float2 *lut, const float *wlut, double *partial,
-                                                       unsigned *fault) {
+                                                       const float2 *lut, const float *wlut, double *partial) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(sizeof(float2), pd, 2, rev_extra_bytes(pd.lut_count), sizeof(float4),
                                    sizeof(float4) << R_MAX_ROT);
@@ -2101,45 +2081,25 @@ __global__ void __launch_bounds__(NT, 2) k_reverse_blk(float *psi, float *lam, i
     const uint32_t rel = d.lut - (uint32_t)pd.lut_begin;
     for (int c = 0; c < (1 << d.r); ++c) wst[rel + c] = __ldg(wlut + d.wlut + c);
   }
-  __shared__ uint64_t bar;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
+  using V = typename Vec16<float>::type;
   const uint64_t ntiles = 1ull << (n - pd.T);
-  uint32_t parity = 0;
   TileWalk tw(blockIdx.x, gridDim.x, pd.umask);
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tw.next()) {
     const uint64_t base = tw.base;
-    const uint32_t nch = 1u << (pd.T - pd.C);
-    const uint32_t bytes = (uint32_t)sizeof(float2) << pd.C;
-    if (threadIdx.x == 0) mbar_expect_tx(&bar, 2 * bytes * nch);
-    for (uint32_t h = threadIdx.x; h < nch; h += NT) {
-      const uint64_t gi = base ^ st.off[h];
-      bulk_g2s(tp + (h << pd.C), reinterpret_cast<const float2 *>(psi) + gi, bytes, &bar);
-      bulk_g2s(tl + (h << pd.C), reinterpret_cast<const float2 *>(lam) + gi, bytes, &bar);
-    }
+    async_load_tile(psi, base, st, tp);
+    async_load_tile(lam, base, st, tl);
     tile_codes(st, ng, t);
-    const bool ok = mbar_wait(&bar, parity, fault);
-    parity ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      mbar_wait(&bar, parity ^ 1u, fault);   // a second bounded wait for the copies in flight
-      break;
-    }
+    cp_async_wait_all();
+    __syncthreads();
     for (int b = nb - 1; b >= 0; --b) {
       reverse_block_any<TT>(tp, tl, st.bs[b], st, rs, pd.lut_begin);
       __syncthreads();
     }
-    fence_proxy_async();
-    __syncthreads();
-    for (uint32_t h = threadIdx.x; h < nch; h += NT) {
-      const uint64_t gi = base ^ st.off[h];
-      bulk_s2g(reinterpret_cast<float2 *>(psi) + gi, tp + (h << pd.C), bytes);
-      bulk_s2g(reinterpret_cast<float2 *>(lam) + gi, tl + (h << pd.C), bytes);
-    }
-    bulk_commit();
-    bulk_wait_read();
-    __syncthreads();
+    store_tile<float, false>(psi, base, st, reinterpret_cast<const V *>(tp));
+    store_tile<float, false>(lam, base, st, reinterpret_cast<const V *>(tl));
+    __syncthreads();   // every thread has read its pieces before the next tiles land
   }
-  bulk_wait_all();
   // per-rotation partials of this CTA: group sums at each group's first rotation, zero elsewhere
   const int nrot = pd.rot_end - pd.rot_begin;
   for (int k = threadIdx.x; k < nrot; k += NT) partial[(size_t)blockIdx.x * RP_MAX + k] = 0.0;
@@ -2466,8 +2426,7 @@ cudaError_t launch_happly(const R *psi, R *lam, int n, const PassDesc &pd, const
     cudaError_t e = prepare(k, worst_smem(sizeof(C2), pd.T, 2, 0, sizeof(C2), al, ham_lut_max<R>()));
     if (e != cudaSuccess) return e;
     const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
-    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), first ? 1 : 0,
-                              fault);
+    k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const C2 *>(lut), first ? 1 : 0);
     return cudaGetLastError();
   }
   PassDesc pq = pd;
@@ -2516,7 +2475,7 @@ cudaError_t launch_reverse(R *psi, R *lam, int n, const PassDesc &pd, const Grou
       if (e != cudaSuccess) return e;
       const unsigned grid = grid_for(1ull << (n - pd.T), blocks_per_sm(k, smem));
       k<<<grid, NT, smem, st>>>(psi, lam, n, pd, groups, blocks, reinterpret_cast<const float2 *>(lut), wlut,
-                                partial, fault);
+                                partial);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       const int nrot = pd.rot_end - pd.rot_begin;
       k_reduce_rot<<<(nrot + 127) / 128, 128, 0, st>>>(partial, (int)grid, nrot, gphi + pd.rot_begin);
