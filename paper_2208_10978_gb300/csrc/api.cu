@@ -1089,8 +1089,11 @@ q2_status q2_batch_energy_grad(int n_requests, const q2_ansatz *const *ansatz, c
   const size_t out_begin = slots[0].out_off;
   const size_t out_bytes = total - out_begin;
   std::vector<double> outs(out_bytes / sizeof(double));
-  Q2_CUDA(cudaMemcpyAsync(outs.data(), ws + out_begin, out_bytes, cudaMemcpyDeviceToHost, st), "read batch");
-  Q2_CUDA(cudaStreamSynchronize(st), "sync");
+  // The kernel is queued: synchronise before any return, so the workspace is never handed back in use.
+  const cudaError_t ce = cudaMemcpyAsync(outs.data(), ws + out_begin, out_bytes, cudaMemcpyDeviceToHost, st);
+  const cudaError_t se = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "read batch");
+  if (se != cudaSuccess) return cuda_fail(se, "sync");
   for (int b = 0; b < n_requests; ++b) {
     const double *o = outs.data() + (slots[b].out_off - out_begin) / sizeof(double);
     energy_out[b] = o[0] / o[1];
