@@ -371,3 +371,30 @@ def test_expectation_chunk_shapes_and_lean_walk_match_oracle(lib, n, T, C):
     if all(int(g["kind"]) in (emu.DIAG, emu.REAL) for g in groups) and all(int(b["d"]) <= 3 for b in blocks):
         e, _ = emu.expectation_lean(psi, n, passes, groups, blocks, lut, NT)
         assert abs(e - e_ref) < 1e-10
+
+
+@pytest.mark.parametrize("n,T,C,amps", [(14, 12, 4, 2), (16, 13, 4, 2), (14, 12, 3, 1), (16, 13, 3, 1)])
+def test_tile_pieces_are_aligned_and_contiguous(lib, n, T, C, amps):
+    """The per-thread tile copies move 16-byte pieces (2 complex64 or 1 complex128 amplitudes):
+    piece v of a tile is local indices v*amps .. v*amps + amps - 1, copied to shared offset 16 v.
+    On real sweep and Hamiltonian plans every piece must start 16-byte aligned in the state and be
+    contiguous there, which holds because tile bases and chunk offsets have their low C bits clear."""
+    w = uccsd_energy(n, n // 2, seed=n)
+    a = w.ansatz
+    rot = emu.rot_plan(lib, n, a.x, a.z, a.angles(w.theta), T, C)[0]
+    ham = emu.ham_plan(lib, n, w.ham.x, w.ham.z, w.ham.c, T, C)[0]
+    checked = 0
+    for pd in list(rot) + list(ham):
+        Cp = int(pd["C"])
+        if int(pd["T"]) < 9:
+            continue   # tiles below 2^9 amplitudes take the guarded plain-load kernels
+        low = (1 << Cp) - 1
+        assert int(pd["umask"]) & low == 0
+        assert all(int(pd["w"][b]) & low == 0 for b in range(Cp, int(pd["T"])))
+        idx = emu.tile_index(n, pd).astype(np.int64)
+        start = idx[:, ::amps]
+        assert np.all(start % amps == 0)
+        for k in range(1, amps):
+            assert np.array_equal(idx[:, k::amps], start + k)
+        checked += 1
+    assert checked > 0
